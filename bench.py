@@ -1,0 +1,434 @@
+"""Benchmark of the spin summation on GB300.
+
+One step = one spin summation B = S(A) over the whole workload, FP64:
+the 3D CCSDT-shaped tensor A[a,b,c,i,j,k] with a,b,c extent 48 and i,j,k
+extent 16 (453M doubles, 3.6 GB), Table II row 1 applied factorized
+(B = (2 - pi213)((2 - pi321 - pi132)(A))), out of place, seeded uniform
+inputs. Metric: effective HBM bandwidth 2 * N * sizeof(double) / time (the
+paper's Eq. 12, in GB/s rather than GiB/s).
+
+Prints one JSON line. `value` is device-timed (CUDA events on the launching
+stream, inputs resident); `e2e` times the same call through the public API
+with pinned host buffers (H2D of A and D2H of B inside the timed region);
+`roofline` relates the kernel to the measured HBM copy bandwidth;
+`cpu_baseline` is the oracle (test infrastructure) on a bounded sample of the
+same workload on the host cores. `--impl reference` times only that oracle.
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own copy of the
+workload with no collective on the data path (weak scaling); barriers and a
+max over ranks bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "3d-spinsum fp64 A[48,48,48,16,16,16] Table-II-row-1 factorized out-of-place"
+SHAPE = (48, 48, 48, 16, 16, 16)
+D = 3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-extra", action="store_true", help="skip the extra per-case lines")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ts, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 - 0.1 <= r[0] <= self.t1 + 0.1]
+        if not inside:  # timed region shorter than the sampling interval: nearest samples
+            mid = ((self.t0 or 0) + (self.t1 or 0)) / 2
+            inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in inside:
+            for name, v in zip(names[1:], r[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1705_06661_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(case: str):
+    """DRAM bytes per launch from the committed ncu summary, only if the
+    kernel sources are unchanged since it was taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    c = rec.get("cases", {}).get(case)
+    return None if c is None else c.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """The oracle as it stands on a bounded sample of the workload: the same
+    operator and permuted extent with the spectator block cut from 48^3 to
+    16^3 (16.8M elements), repeated for about `seconds`."""
+    import oracle
+    import workloads as wl
+    shape = (16, 16, 16, 16, 16, 16)
+    A = wl.uniform(1, shape)
+    B = np.empty(shape, order="F")
+    coef = wl.table2(1)
+    n = A.size
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.spinsum(A, D, coef, factorized=True, B=B)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(2 * n * 8 * reps / dt / 1e9, 3), "unit": "GB/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"A[16,16,16,16,16,16] ({n} doubles), same operator/mode, {reps} runs in {dt:.1f} s"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workloads as wl
+    shape = (16, 16, 16, 16, 16, 16)      # bounded sample of the workload per step
+    A = wl.uniform(1, shape)
+    B = np.empty(shape, order="F")
+    coef = wl.table2(1)
+    for _ in range(args.warmup):
+        oracle.spinsum(A, D, coef, factorized=True, B=B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spinsum(A, D, coef, factorized=True, B=B)
+    dt = time.perf_counter() - t0
+    val = 2 * A.size * 8 * args.steps / dt / 1e9
+    sample = f"A[16,16,16,16,16,16] ({A.size} doubles) per step, same operator and mode"
+    print(json.dumps({
+        "impl": "reference", "metric": "spin-summation effective HBM GB/s (2*N*bytes/time)", "value": round(val, 3),
+        "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (SplitMix64 seed 1, uniform [-1,1))",
+        "config": {"workload": WORKLOAD, "reference_sample": sample},
+        "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "sample": sample, "value": round(val, 3),
+                         "unit": "GB/s"},
+        "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def time_steps(fn, steps, stream, world):
+    import torch
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def best_of(fn, reps, stream):
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return min(ts), float(np.median(ts))
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1705_06661_gb300 as ss
+    import workloads as wl
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "of measured (MEASURED_PEAKS.json hbm_gbs, torch copy)" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or 6800.0
+
+    # ---- inputs, resident in HBM ----
+    A_host = wl.uniform(1, SHAPE)                      # column-major float64, 3.6 GB
+    N = A_host.size
+    A = ss.colmajor_empty(SHAPE, device=dev)
+    A.copy_(torch.from_numpy(A_host).to(dev))
+    B = ss.colmajor_like(A)
+    coef = wl.table2(1)
+    step = lambda: ss.spinsum(A, coef, d=D, out=B, factorized=True)  # noqa: E731
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ss.spinsum_check_status(stream.cuda_stream)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ss.spinsum_launch_count(reset=True)
+    clocks.mark("t0")
+    dt = time_steps(step, args.steps, stream, world)
+    clocks.mark("t1")
+    launches = ss.spinsum_launch_count(reset=True)
+    clocks.stop()
+    dt_max = allmax(world, dt)
+    bytes_step = 2 * N * 8
+    value = world * bytes_step * args.steps / dt_max / 1e9
+    ms_step = dt_max / args.steps * 1e3
+    per_launch_s = dt / max(launches, 1)
+    achieved = bytes_step / per_launch_s / 1e9 if launches == args.steps else bytes_step * args.steps / dt / 1e9
+    ss.spinsum_check_status(stream.cuda_stream)
+
+    # ---- end to end through the public API with pinned host buffers ----
+    A_pin = torch.from_numpy(A_host).pin_memory() if True else None
+    B_pin = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(6)))
+    A_pin_cm = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(6)))
+    A_pin_cm.copy_(A_pin)
+    del A_pin
+
+    def e2e_step():
+        A.copy_(A_pin_cm, non_blocking=True)
+        ss.spinsum(A, coef, d=D, out=B, factorized=True)
+        B_pin.copy_(B, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    dt_e2e = allmax(world, time_steps(e2e_step, e2e_steps, stream, world))
+    e2e_val = world * bytes_step * e2e_steps / dt_e2e / 1e9
+    # the result that came back is the result computed on the device
+    assert torch.equal(B_pin[:2, :2, :2, :3, :3, :3], B[:2, :2, :2, :3, :3, :3].cpu())
+
+    # ---- extra cases: other modes and the 4D workload (not the headline) ----
+    extra = []
+    if not args.no_extra and rank == 0:
+        reps = 10
+        cases = [
+            # in place, repeated application grows the dominant component by the spectral radius of
+            # the operator (12 for row 1); alpha = 2^-4 keeps the values bounded across repetitions
+            ("3d row1 factorized in-place (alpha=2^-4)",
+             lambda: ss.spinsum(A, coef, d=D, inplace=True, factorized=True, alpha=0.0625)),
+            ("3d row1 expanded out-of-place", lambda: ss.spinsum(A, coef, d=D, out=B)),
+            ("3d random-set expanded out-of-place", lambda: ss.spinsum(A, wl.random_coef(3, 102), d=D, out=B)),
+            ("3d row1 strict-fp64 out-of-place", lambda: ss.spinsum(A, coef, d=D, out=B, factorized=True,
+                                                                    strict=True)),
+        ]
+        for name, fn in cases:
+            for _ in range(2):
+                fn()
+            mn, md = best_of(fn, reps, stream)
+            extra.append({"case": name, "GB/s": round(bytes_step / mn / 1e9, 1), "ms_min": round(mn * 1e3, 4),
+                          "ms_median": round(md * 1e3, 4), "frac": round(bytes_step / mn / 1e9 / hbm_peak, 4)})
+        del A_pin_cm, B_pin
+        A32 = ss.colmajor_empty(SHAPE, dtype=torch.float32, device=dev)
+        A32.copy_(A)
+        B32 = ss.colmajor_like(A32)
+        fn = lambda: ss.spinsum(A32, coef, d=D, out=B32, factorized=True)  # noqa: E731
+        fn()
+        mn, md = best_of(fn, reps, stream)
+        extra.append({"case": "3d row1 factorized fp32-storage", "GB/s": round(2 * N * 4 / mn / 1e9, 1),
+                      "ms_min": round(mn * 1e3, 4), "frac": round(2 * N * 4 / mn / 1e9 / hbm_peak, 4)})
+        del A32, B32, A, B
+        torch.cuda.empty_cache()
+        shape4 = (12,) * 8
+        A4 = ss.colmajor_empty(shape4, device=dev)
+        A4.copy_(torch.from_numpy(wl.uniform(2, shape4)).to(dev))
+        B4 = ss.colmajor_like(A4)
+        n4 = A4.numel()
+        for name, c4, kw in [("4d row5 factorized out-of-place", wl.table2(5), {"factorized": True}),
+                             ("4d row5 factorized in-place (alpha=2^-6)", wl.table2(5),
+                              {"factorized": True, "inplace": True, "alpha": 2.0 ** -6}),
+                             ("4d row6 factorized out-of-place", wl.table2(6), {"factorized": True}),
+                             ("4d row18 out-of-place", wl.table2(18), {}),
+                             ("4d random-set expanded out-of-place", wl.random_coef(4, 103), {})]:
+            if kw.get("inplace"):
+                fn = lambda c4=c4, kw=kw: ss.spinsum(A4, c4, d=4, **kw)  # noqa: E731
+            else:
+                fn = lambda c4=c4, kw=kw: ss.spinsum(A4, c4, d=4, out=B4, **kw)  # noqa: E731
+            for _ in range(2):
+                fn()
+            mn, md = best_of(fn, reps, stream)
+            extra.append({"case": name, "GB/s": round(2 * n4 * 8 / mn / 1e9, 1), "ms_min": round(mn * 1e3, 4),
+                          "ms_median": round(md * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
+        ss.spinsum_check_status(stream.cuda_stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        out = {
+            "metric": "spin-summation effective HBM GB/s (2*N*bytes/time)",
+            "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (SplitMix64 seed 1, uniform [-1,1)), inputs resident in HBM",
+            "config": {"workload": WORKLOAD, "elements": N, "bytes_per_step": bytes_step,
+                       "l2": "inputs larger than L2 (3.6 GB per tensor), no flush",
+                       "parallelism": f"replicas x{world} (one full problem per GPU)"},
+            "element_updates_per_s": round(world * N * args.steps / dt_max, 1),
+            "gibps_eq12": round(world * bytes_step * args.steps / dt_max / 2 ** 30, 1),
+            "frac_of_8TBps": round(value / 8000.0, 4),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
+                         "traffic": ncu_traffic("3d-row1-factorized-oop"),
+                         "algorithmic_bytes_per_launch": bytes_step},
+            "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": N * 8,
+                    "d2h_bytes_per_step": N * 8, "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+            "paper_context": "Alg. 6 speedups over NCC 2.4-5.5x on 2x Xeon E5-2680 v3 (FP64); no absolute numbers",
+            "cases": extra,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * spinsum.h -- C-ABI of the GB300 spin-summation library.
+ *
+ * The operation (Def. 3, Eq. 4 of Springer, Matthews & Bientinesi, "Spin
+ * Summations: A High-Performance Perspective", arXiv 1705.06661):
+ *
+ *   B = alpha * sum_{sigma in S_d} a_sigma * pi_sigma(A) + beta * B
+ *
+ * over one group of d permuted indices of a tensor that also carries d
+ * spectator indices (CCSDT: d = 3, A[a,b,c,i,j,k]; CCSDTQ: d = 4,
+ * A[a,b,c,d,i,j,k,l]). pi_phi acts on the permuted group as in Def. 1-2
+ * (Eq. 1-3): pi_phi(A)[s, i_1..i_d] = A[s, i_phi(1), ..., i_phi(d)].
+ *
+ * Coefficients. `coef` holds `nfactors` rows of d! doubles each; the columns
+ * are the permutations of S_d in lexicographic one-line order, identity first
+ * (for d = 3: 123, 132, 213, 231, 312, 321 -- the order of Algorithms 2 and 4).
+ * The rows are a factor chain F_1 .. F_k meaning B = F_1(F_2(...F_k(A)))
+ * (Def. 4, Eq. 5-6); composition follows Eq. 9-10: pi_phi(pi_psi(A)) =
+ * pi_{phi o psi}(A). With one row the chain is a plain coefficient vector.
+ *
+ * Tensor layout. Every index has an extent and an element stride (int64,
+ * counted in elements, not bytes). Indices 0..d-1 are the spectators, indices
+ * d..2d-1 the permuted group; the d permuted extents must be equal (Sec. 3.1).
+ * Column-major storage with the spectators fastest is the fast layout: each
+ * permuted tuple then owns a contiguous run of ext[0]*..*ext[d-1] elements.
+ * The paper's own N^d layout is spectator extents 1 with the permuted group at
+ * strides 1, N, N^2 (, N^3); any other non-overlapping strides also work.
+ *
+ * Ownership. The caller owns every buffer. A and B are device pointers; calls
+ * are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream)
+ * and allocate nothing. Coefficients, extents and strides are host memory,
+ * read during the call only.
+ *
+ * Errors. Every entry point returns SPINSUM_OK (0) or a negative status and
+ * never aborts, exits or traps the GPU. spinsum_last_error() gives a message
+ * for the calling thread's last failure. Device-side failures (a bounded wait
+ * that ran out, an element outside the fast path's range that could not be
+ * handled) set a device status word that spinsum_check_status() reads.
+ */
+#ifndef SPINSUM_H
+#define SPINSUM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* spinsum_stream_t; /* same type as cudaStream_t */
+
+enum spinsum_status {
+  SPINSUM_OK = 0,
+  SPINSUM_ERR_ARG = -1,         /* bad extent, stride, pointer, dtype, mode or coefficient */
+  SPINSUM_ERR_ALIAS = -2,       /* A and B overlap without inplace = 1 (or inplace with A != B) */
+  SPINSUM_ERR_UNSUPPORTED = -3, /* valid request this build does not implement */
+  SPINSUM_ERR_CUDA = -4,        /* a CUDA runtime call failed (message has the CUDA error) */
+  SPINSUM_ERR_TIMEOUT = -5,     /* a device-side bounded wait ran out */
+  SPINSUM_ERR_DEVICE = -6       /* another device-side check failed */
+};
+
+enum spinsum_dtype { SPINSUM_F64 = 0, SPINSUM_F32 = 1 };
+
+/* mode bits */
+enum spinsum_mode {
+  SPINSUM_EXPANDED = 0,   /* multiply the chain out on the host (product rule), one pass of d!-term sums */
+  SPINSUM_FACTORIZED = 1, /* apply the factors stage by stage on chip, innermost first (Def. 4) */
+  SPINSUM_ADJOINT = 2,    /* apply the transpose S^T = F_k^T ... F_1^T, F^T(sigma) = F(sigma^-1) */
+  SPINSUM_STRICT = 4      /* FP64 only: native FP64 arithmetic in the reference order (lex sigma,
+                             multiply then add, no FMA), bit-identical to a plain loop nest */
+};
+
+/*
+ * spinsum_3d -- 3D spin summation on a 6-index tensor (Def. 3 with d = 3).
+ *
+ * dtype : SPINSUM_F64 (double in, double out) or SPINSUM_F32 (float in, float
+ *         out, float accumulation).
+ * ext   : 6 extents; ext[0..2] spectators a,b,c; ext[3..5] permuted i,j,k,
+ *         ext[3] == ext[4] == ext[5].
+ * A,lda : input tensor and its 6 element strides.
+ * B,ldb : output tensor and its 6 element strides.
+ * coef  : nfactors x 6 doubles (see above); 1 <= nfactors <= 8; finite.
+ * mode  : SPINSUM_EXPANDED or SPINSUM_FACTORIZED, optionally | SPINSUM_ADJOINT,
+ *         | SPINSUM_STRICT.
+ * alpha, beta : B = alpha * S(A) + beta * B_old; beta == 0 never reads B.
+ * inplace : 1 computes A = alpha * S(A) + beta * A (Sec. 4.6.5); then B must
+ *           equal A and ldb equal lda. 0 requires A and B not to overlap.
+ * stream : cudaStream_t to launch on.
+ *
+ * FP64 arithmetic. With integer coefficients (up to a common power-of-two
+ * scale) and a chain 1-norm below 128, the sums run in exact fixed-point
+ * integer arithmetic on a per-element grid of 2^-48 of the largest input of
+ * the permutation orbit: integer-valued inputs give exact results, other
+ * inputs are within 2^-47 * sum|a| * max|A| (plus the final rounding).
+ * Otherwise, or with SPINSUM_STRICT, native FP64 in the reference order.
+ */
+int spinsum_3d(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
+               const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream);
+
+/* spinsum_4d -- 4D spin summation on an 8-index tensor (Def. 3 with d = 4):
+ * ext[0..3] spectators a,b,c,d; ext[4..7] permuted i,j,k,l (all equal);
+ * coef is nfactors x 24 doubles. Otherwise as spinsum_3d. */
+int spinsum_4d(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
+               const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream);
+
+/*
+ * Batched plans: many independent spin summations (uneven extents, mixed d,
+ * mixed coefficient sets) run by one persistent kernel launch.
+ *
+ * spinsum_problem describes one summation exactly as the arguments of
+ * spinsum_3d / spinsum_4d do (d = 3 uses the first 6 entries of ext/lda/ldb).
+ * spinsum_plan_create validates every problem, builds the device work list
+ * (the plan allocates and owns that device memory until destroyed), copies the
+ * coefficients, and picks tile sizes with its autotuner (which times
+ * candidates on `stream` and may therefore run the problems: inputs must be
+ * valid and in-place problems are restored only if `allow_tuning_runs` is 0,
+ * in which case a fixed heuristic is used). dtype applies to all problems.
+ * spinsum_plan_execute launches the whole batch as one kernel on `stream`;
+ * it allocates nothing and may be captured in a CUDA graph.
+ */
+typedef struct spinsum_problem {
+  int d;            /* 3 or 4 */
+  int64_t ext[8];   /* d spectators then d permuted extents */
+  const void* A;
+  int64_t lda[8];
+  void* B;
+  int64_t ldb[8];
+  const double* coef; /* nfactors x d! */
+  int nfactors;
+  int mode;
+  double alpha;
+  double beta;
+  int inplace;
+} spinsum_problem;
+
+typedef struct spinsum_plan spinsum_plan;
+
+int spinsum_plan_create(spinsum_plan** plan, const spinsum_problem* problems, int nproblems, int dtype,
+                        int allow_tuning_runs, spinsum_stream_t stream);
+int spinsum_plan_execute(spinsum_plan* plan, spinsum_stream_t stream);
+int spinsum_plan_destroy(spinsum_plan* plan);
+/* description of the plan's tuning choice, e.g. "vec=2 block=256 split=1" */
+const char* spinsum_plan_describe(const spinsum_plan* plan);
+
+/* Synchronizes `stream`, then reads and clears the device status word:
+ * SPINSUM_OK, SPINSUM_ERR_TIMEOUT or SPINSUM_ERR_DEVICE. */
+int spinsum_check_status(spinsum_stream_t stream);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* spinsum_last_error(void);
+
+/* Number of kernel launches the calling thread has issued through this
+ * library since the last reset (for launch accounting in benchmarks). */
+int64_t spinsum_launch_count(int reset);
+
+/* Library version string. */
+const char* spinsum_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPINSUM_H */

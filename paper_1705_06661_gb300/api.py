@@ -1,0 +1,112 @@
+"""Torch-facing API. PyTorch supplies device memory and streams only; every
+step of the spin summation runs in the CUDA library behind the C-ABI.
+
+Tensors use their own strides: dimension order is (spectators..., permuted...)
+and any non-overlapping layout works. The fast layout is column-major with
+the spectators fastest (``colmajor_empty``), i.e. A[a,b,c,i,j,k] stored with
+a fastest, as in the paper's column-major convention (Sec. 3.1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import _binding as _b
+
+
+def colmajor_empty(shape, dtype=torch.float64, device="cuda") -> torch.Tensor:
+    """Dense column-major tensor (first index fastest) with logical shape `shape`."""
+    shape = tuple(int(s) for s in shape)
+    t = torch.empty(tuple(reversed(shape)), dtype=dtype, device=device)
+    return t.permute(*reversed(range(len(shape))))
+
+
+def colmajor_like(x: torch.Tensor) -> torch.Tensor:
+    return colmajor_empty(x.shape, dtype=x.dtype, device=x.device)
+
+
+def to_colmajor(x: torch.Tensor) -> torch.Tensor:
+    y = colmajor_like(x)
+    y.copy_(x)
+    return y
+
+
+def _coef_chain(coef, d: int) -> np.ndarray:
+    c = np.asarray(coef.detach().cpu().numpy() if isinstance(coef, torch.Tensor) else coef, dtype=np.float64)
+    if c.ndim == 1:
+        c = c[None, :]
+    if c.ndim != 2 or c.shape[1] != math.factorial(d):
+        raise ValueError(f"coefficients must have shape [nfactors, {math.factorial(d)}]")
+    return np.ascontiguousarray(c)
+
+
+def _dims(x: torch.Tensor, d: int):
+    """extents and element strides in ABI order (d spectators, d permuted);
+    a tensor with only the d permuted dimensions gets spectator extents 1."""
+    if x.dim() == 2 * d:
+        return list(x.shape), list(x.stride())
+    if x.dim() == d:
+        return [1] * d + list(x.shape), [1] * d + list(x.stride())
+    raise ValueError(f"expected a tensor with {d} or {2 * d} dimensions, got {x.dim()}")
+
+
+def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | None = None,
+            factorized: bool = False, adjoint: bool = False, strict: bool = False, alpha: float = 1.0,
+            beta: float = 0.0, inplace: bool = False, stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """B = alpha * S(A) + beta * B (or A in place), S the spin summation of the
+    coefficient chain `coef` ([nfactors, d!], lexicographic permutation order)."""
+    if d is None:
+        d = A.dim() // 2
+    if d not in (3, 4):
+        raise ValueError("d must be 3 or 4")
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.dtype == torch.float64:
+        dtype = _b.SPINSUM_F64
+    elif A.dtype == torch.float32:
+        dtype = _b.SPINSUM_F32
+    else:
+        raise TypeError("A must be float64 or float32")
+    c = _coef_chain(coef, d)
+    if inplace:
+        out = A
+    elif out is None:
+        out = colmajor_like(A) if beta == 0.0 else None
+        if out is None:
+            raise ValueError("beta != 0 needs an output tensor")
+    if out.dtype != A.dtype or out.device != A.device or tuple(out.shape) != tuple(A.shape):
+        raise ValueError("out must match A in dtype, device and shape")
+    ext, lda = _dims(A, d)
+    _, ldb = _dims(out, d)
+    mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
+        | (_b.SPINSUM_STRICT if strict else 0)
+    st = (stream or torch.cuda.current_stream(A.device)).cuda_stream
+    fn = _b.spinsum_3d if d == 3 else _b.spinsum_4d
+    with torch.cuda.device(A.device):
+        fn(dtype, ext, A.data_ptr(), lda, out.data_ptr(), ldb, c, c.shape[0], mode, alpha, beta, int(inplace), st)
+    return out
+
+
+class SpinSumFunction(torch.autograd.Function):
+    """Differentiable spin summation. The operator is linear, so the gradient
+    of B = alpha S(A) is alpha S^T(gB), S^T = sum a_sigma pi_{sigma^-1} for one
+    factor and F_k^T ... F_1^T for a chain; the backward pass is the same orbit
+    kernel with SPINSUM_ADJOINT."""
+
+    @staticmethod
+    def forward(ctx, A, coef, d, factorized, alpha):
+        ctx.coef, ctx.d, ctx.factorized, ctx.alpha = coef, d, factorized, alpha
+        return spinsum(A, coef, d=d, factorized=factorized, alpha=alpha)
+
+    @staticmethod
+    def backward(ctx, gB):
+        gA = spinsum(gB, ctx.coef, d=ctx.d, factorized=ctx.factorized, adjoint=True, alpha=ctx.alpha)
+        return gA, None, None, None, None
+
+
+def spinsum_autograd(A: torch.Tensor, coef, *, d: int | None = None, factorized: bool = False,
+                     alpha: float = 1.0) -> torch.Tensor:
+    d = d if d is not None else A.dim() // 2
+    return SpinSumFunction.apply(A, _coef_chain(coef, d), d, factorized, float(alpha))

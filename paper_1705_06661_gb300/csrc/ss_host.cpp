@@ -1,0 +1,517 @@
+// Host side of the spin-summation library: argument checks, coefficient
+// algebra (product rule, adjoint, orbit matrices), choice of arithmetic and
+// kernel, and the extern "C" entry points declared in include/spinsum.h.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/spinsum.h"
+#include "ss_internal.h"
+
+namespace ss {
+cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st);
+cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st);
+cudaError_t read_and_clear_status(int* out);
+}  // namespace ss
+
+using namespace ss;
+
+namespace {
+
+thread_local std::string t_err;
+thread_local int64_t t_launches = 0;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SPINSUM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// permutation group tables (lexicographic order, 0-based images)
+// ---------------------------------------------------------------------------
+struct Group {
+  int d = 0, n = 0;
+  int p[24][4] = {};
+  int inv[24] = {};       // index of the inverse permutation
+  int comp[24][24] = {};  // index of phi o psi, (phi o psi)(m) = phi(psi(m))
+};
+
+Group make_group(int d) {
+  Group g;
+  g.d = d;
+  int a[4] = {0, 1, 2, 3};
+  for (;;) {
+    for (int m = 0; m < d; m++) g.p[g.n][m] = a[m];
+    g.n++;
+    int i = d - 2;
+    while (i >= 0 && a[i] > a[i + 1]) i--;
+    if (i < 0) break;
+    int j = d - 1;
+    while (a[j] < a[i]) j--;
+    std::swap(a[i], a[j]);
+    for (int x = i + 1, y = d - 1; x < y; x++, y--) std::swap(a[x], a[y]);
+  }
+  auto find = [&](const int* q) {
+    for (int k = 0; k < g.n; k++) {
+      bool same = true;
+      for (int m = 0; m < d; m++) same = same && g.p[k][m] == q[m];
+      if (same) return k;
+    }
+    return -1;
+  };
+  for (int k = 0; k < g.n; k++) {
+    int q[4] = {};
+    for (int m = 0; m < d; m++) q[g.p[k][m]] = m;
+    g.inv[k] = find(q);
+    for (int l = 0; l < g.n; l++) {
+      int c[4] = {};
+      for (int m = 0; m < d; m++) c[m] = g.p[k][g.p[l][m]];
+      g.comp[k][l] = find(c);
+    }
+  }
+  return g;
+}
+
+const Group& group(int d) {
+  static const Group g3 = make_group(3), g4 = make_group(4);
+  return d == 3 ? g3 : g4;
+}
+
+// product of a chain F_1 .. F_k (B = F_1(...F_k(A))): left fold, each entry
+// summed over (phi, psi) pairs in lexicographic order, zero terms skipped.
+std::vector<double> expand_chain(const Group& g, const std::vector<std::vector<double>>& chain) {
+  std::vector<double> P = chain[0];
+  for (size_t f = 1; f < chain.size(); f++) {
+    std::vector<double> Q(g.n, 0.0);
+    for (int a = 0; a < g.n; a++) {
+      if (P[a] == 0.0) continue;
+      for (int b = 0; b < g.n; b++) {
+        if (chain[f][b] == 0.0) continue;
+        double prod = P[a] * chain[f][b];
+        Q[g.comp[a][b]] = Q[g.comp[a][b]] + prod;
+      }
+    }
+    P = Q;
+  }
+  return P;
+}
+
+// smallest e >= -40 such that every c * 2^e is an integer of magnitude < 2^24;
+// returns false if there is none
+bool int_scale(const std::vector<double>& c, int* e_out) {
+  for (int e = -40; e <= 60; e++) {
+    bool ok = true;
+    for (double v : c) {
+      double s = std::ldexp(v, e);
+      if (std::fabs(s) >= 16777216.0 || s != std::floor(s)) { ok = false; break; }
+    }
+    if (ok) { *e_out = e; return true; }
+  }
+  return false;
+}
+
+// integer exponent a with alpha == +-2^a, else false
+bool pow2(double x, int* a) {
+  if (x == 0.0 || !std::isfinite(x)) return false;
+  int e;
+  double m = std::frexp(std::fabs(x), &e);
+  if (m != 0.5) return false;
+  *a = e - 1;
+  return true;
+}
+
+int64_t binom(int n, int k) {
+  if (n < k || k < 0) return 0;
+  int64_t r = 1;
+  for (int i = 0; i < k; i++) r = r * (n - i) / (i + 1);
+  return r;
+}
+
+template <int D>
+int pattern_nd(int P) { return make_pattern<D>(P).nd; }
+template <int D>
+int pattern_m(int P) { return make_pattern<D>(P).m; }
+
+int nd_of(int d, int P) { return d == 3 ? pattern_nd<3>(P) : pattern_nd<4>(P); }
+
+// dense expanded orbit matrices of the degenerate patterns
+template <int D>
+void fill_mp(const std::vector<long long>& a, int* mp) {
+  for (int P = 1; P < npatterns(D); P++) {
+    const Pattern<D> pt = make_pattern<D>(P);
+    int* M = mp + mp_offset<D>(P);
+    for (int u = 0; u < pt.m; u++)
+      for (int v = 0; v < pt.m; v++) M[u * pt.m + v] = 0;
+    for (int u = 0; u < pt.m; u++)
+      for (int s = 0; s < fact(D); s++) M[u * pt.m + pt.idx[u][s]] += (int)a[s];
+  }
+}
+
+struct Request {
+  int d, dtype;
+  const int64_t* ext;
+  const void* A;
+  const int64_t* lda;
+  void* B;
+  const int64_t* ldb;
+  const double* coef;
+  int nfactors, mode;
+  double alpha, beta;
+  int inplace;
+};
+
+// byte span [lo, hi) touched by a strided tensor
+void span(int n, const int64_t* ext, const int64_t* ld, const void* base, size_t es, uintptr_t* lo,
+          uintptr_t* hi) {
+  int64_t mx = 0;
+  for (int k = 0; k < n; k++) mx += (ext[k] - 1) * ld[k];
+  *lo = (uintptr_t)base;
+  *hi = (uintptr_t)base + (uintptr_t)((mx + 1) * (int64_t)es);
+}
+
+struct Launch {
+  KParams kp;
+  int ar = AR_STRICT;
+  int kernel = 0;  // 0 = K1, 1 = KG
+  int vec = 1;
+  bool empty = false;
+};
+
+int plan_one(const Request& r, Launch* L) {
+  const int d = r.d;
+  if (d != 3 && d != 4) return fail(SPINSUM_ERR_ARG, "d must be 3 or 4");
+  if (r.dtype != SPINSUM_F64 && r.dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", r.dtype);
+  if (r.mode & ~(SPINSUM_FACTORIZED | SPINSUM_ADJOINT | SPINSUM_STRICT))
+    return fail(SPINSUM_ERR_ARG, "unknown mode bits 0x%x", r.mode);
+  if ((r.mode & SPINSUM_STRICT) && r.dtype != SPINSUM_F64)
+    return fail(SPINSUM_ERR_ARG, "SPINSUM_STRICT applies to FP64 only");
+  if (!r.ext || !r.lda || !r.ldb) return fail(SPINSUM_ERR_ARG, "null extent or stride array");
+  if (r.nfactors < 1 || r.nfactors > MAXSTAGE) return fail(SPINSUM_ERR_ARG, "nfactors must be 1..%d", MAXSTAGE);
+  if (!r.coef) return fail(SPINSUM_ERR_ARG, "null coefficient array");
+  if (!std::isfinite(r.alpha) || !std::isfinite(r.beta)) return fail(SPINSUM_ERR_ARG, "alpha/beta must be finite");
+  const int nidx = 2 * d;
+  int64_t total = 1;
+  for (int k = 0; k < nidx; k++) {
+    if (r.ext[k] < 0) return fail(SPINSUM_ERR_ARG, "negative extent at index %d", k);
+    total *= r.ext[k];
+  }
+  const int O = (int)r.ext[d];
+  for (int k = d; k < nidx; k++)
+    if (r.ext[k] != r.ext[d]) return fail(SPINSUM_ERR_ARG, "permuted extents must be equal (index %d)", k);
+  if (r.ext[d] > 4096) return fail(SPINSUM_ERR_UNSUPPORTED, "permuted extent above 4096");
+  const Group& g = group(d);
+  for (int i = 0; i < r.nfactors * g.n; i++)
+    if (!std::isfinite(r.coef[i])) return fail(SPINSUM_ERR_ARG, "non-finite coefficient at %d", i);
+  for (int k = 0; k < nidx; k++)
+    if (r.lda[k] < 0 || r.ldb[k] < 0) return fail(SPINSUM_ERR_UNSUPPORTED, "negative strides are not supported");
+  if (total == 0) { L->empty = true; return SPINSUM_OK; }
+  if (!r.A || !r.B) return fail(SPINSUM_ERR_ARG, "null tensor pointer");
+  const size_t es = r.dtype == SPINSUM_F64 ? 8 : 4;
+  if (((uintptr_t)r.A % es) || ((uintptr_t)r.B % es)) return fail(SPINSUM_ERR_ARG, "misaligned tensor pointer");
+  if (r.inplace) {
+    if (r.A != r.B) return fail(SPINSUM_ERR_ALIAS, "inplace requires A == B");
+    for (int k = 0; k < nidx; k++)
+      if (r.lda[k] != r.ldb[k]) return fail(SPINSUM_ERR_ALIAS, "inplace requires lda == ldb");
+  } else {
+    uintptr_t alo, ahi, blo, bhi;
+    span(nidx, r.ext, r.lda, r.A, es, &alo, &ahi);
+    span(nidx, r.ext, r.ldb, r.B, es, &blo, &bhi);
+    if (alo < bhi && blo < ahi) return fail(SPINSUM_ERR_ALIAS, "A and B overlap (use inplace = 1 for A == B)");
+  }
+
+  // ---- coefficients: chain in application order (innermost first) ----
+  std::vector<std::vector<double>> chain(r.nfactors, std::vector<double>(g.n));
+  for (int f = 0; f < r.nfactors; f++)
+    for (int s = 0; s < g.n; s++) chain[f][s] = r.coef[f * g.n + s];
+  if (r.mode & SPINSUM_ADJOINT) {
+    // (F_1 ... F_k)^T = F_k^T ... F_1^T, F^T[sigma] = F[sigma^-1]
+    std::vector<std::vector<double>> t(r.nfactors, std::vector<double>(g.n));
+    for (int f = 0; f < r.nfactors; f++)
+      for (int s = 0; s < g.n; s++) t[f][s] = chain[r.nfactors - 1 - f][g.inv[s]];
+    chain = t;
+  }
+  const bool factorized = (r.mode & SPINSUM_FACTORIZED) && r.nfactors > 1;
+  std::vector<std::vector<double>> stages;  // application order
+  const std::vector<double> full = expand_chain(g, chain);
+  if (factorized) {
+    for (int f = r.nfactors - 1; f >= 0; f--) stages.push_back(chain[f]);
+  } else {
+    stages.push_back(full);
+  }
+
+  KParams& kp = L->kp;
+  memset(&kp, 0, sizeof kp);
+  kp.A = r.A;
+  kp.B = r.B;
+  kp.O = O;
+  kp.alpha = r.alpha;
+  kp.beta = r.beta;
+  kp.nstage = (int)stages.size();
+  kp.flags = r.beta != 0.0 ? KF_BETA : 0;
+  for (int st = 0; st < kp.nstage; st++)
+    for (int s = 0; s < g.n; s++) kp.cd[st][s] = stages[st][s];
+  for (int k = 0; k < d; k++) {
+    kp.lda[k] = r.lda[d + k];
+    kp.ldb[k] = r.ldb[d + k];
+  }
+
+  // ---- arithmetic ----
+  if (r.dtype == SPINSUM_F32) {
+    L->ar = AR_F32;
+  } else if (r.mode & SPINSUM_STRICT) {
+    L->ar = AR_STRICT;
+  } else {
+    L->ar = AR_STRICT;
+    // exact fixed-point path: integer stage coefficients up to a power-of-two scale
+    // in exact arithmetic a chain and its expansion give identical results,
+    // so a chain longer than the exact core unrolls is applied expanded
+    std::vector<std::vector<double>> istages = stages;
+    if (istages.size() > (size_t)MAXSTAGE_EXACT) istages.assign(1, full);
+    bool ok = true;
+    int escale = 0;
+    double Lnorm = 1.0;
+    std::vector<std::vector<long long>> ist(istages.size());
+    for (size_t st = 0; st < istages.size() && ok; st++) {
+      int e;
+      if (!int_scale(istages[st], &e)) { ok = false; break; }
+      escale += e;
+      double n1 = 0;
+      for (int s = 0; s < g.n; s++) {
+        ist[st].push_back((long long)std::ldexp(istages[st][s], e));
+        n1 += std::fabs(std::ldexp(istages[st][s], e));
+      }
+      Lnorm *= n1;
+    }
+    int a = 0;
+    const bool apow2 = pow2(r.alpha, &a);
+    if (ok && Lnorm >= 1.0 && Lnorm <= 127.0) {
+      int W = 26;
+      while (W > 0 && Lnorm * std::ldexp(1.0, W) > 2147483647.0) W--;
+      if (2 * W >= 48) {
+        // expanded integer coefficients for the orbit matrices: product of the scaled stages
+        std::vector<long long> ex(g.n, 0);
+        {
+          std::vector<long long> P = ist[0];
+          for (size_t st = 1; st < ist.size(); st++) {
+            std::vector<long long> Q(g.n, 0);
+            // stage st is applied after stage st-1: operator = S_st o S_(st-1)
+            for (int x = 0; x < g.n; x++)
+              for (int y = 0; y < g.n; y++) Q[g.comp[x][y]] += ist[st][x] * P[y];
+            P = Q;
+          }
+          ex = P;
+        }
+        const bool neg = apow2 && r.alpha < 0;
+        int aexp = -escale + (apow2 ? a : 0);
+        int kdrop = 0;
+        const double ymax = Lnorm * (std::ldexp(1.0, 2 * W) + std::ldexp(1.0, W));
+        while (ymax / std::ldexp(1.0, kdrop) + 1.0 >= std::ldexp(1.0, 50)) kdrop++;
+        const int cshift = 53 - 2 * W + kdrop + aexp;
+        const int emin = std::max(64, 1 - cshift), emax = std::min(2046, 2046 - cshift);
+        if (emin <= emax) {
+          L->ar = AR_EXACT;
+          kp.nci = (int)ist.size();
+          kp.W = W;
+          kp.s0 = 53 - 2 * W;
+          kp.kdrop = kdrop;
+          kp.rnd = kdrop ? (1LL << (kdrop - 1)) : 0;
+          if (kdrop) kp.flags |= KF_KDROP;
+          if (!apow2) kp.flags |= KF_ALPHA_MUL;
+          kp.cexp = (int)((unsigned)cshift << 20) + 0x80000;
+          kp.emin = (unsigned)emin << 20;
+          kp.emax = (unsigned)emax << 20;
+          // sign of alpha folded into the last stage / the orbit matrices
+          for (size_t st = 0; st < ist.size(); st++)
+            for (int s = 0; s < g.n; s++)
+              kp.ci[st][s] = (int)((neg && st + 1 == ist.size()) ? -ist[st][s] : ist[st][s]);
+          if (neg)
+            for (auto& v : ex) v = -v;
+          if (d == 3) fill_mp<3>(ex, kp.mp);
+          else fill_mp<4>(ex, kp.mp);
+        }
+      }
+    }
+  }
+
+  // ---- layout and launch shape ----
+  int64_t S = 1;
+  bool dense = true;
+  for (int k = 0; k < d; k++) {
+    if (r.ext[k] != 1 && (r.lda[k] != S || r.ldb[k] != S)) dense = false;
+    S *= r.ext[k];
+  }
+  kp.S = S;
+  kp.nspec = d;
+  for (int k = 0; k < d; k++) {
+    kp.sext[k] = r.ext[k];
+    kp.slda[k] = r.lda[k];
+    kp.sldb[k] = r.ldb[k];
+  }
+  const int np = npatterns(d);
+  for (int p = 0; p < np; p++) kp.norb[p] = binom(O, nd_of(d, p));
+  if (dense && S >= 64) {
+    L->kernel = 0;
+    int vec = 1;
+    const int want = (r.dtype == SPINSUM_F64) ? (d == 3 ? 2 : 1) : (d == 3 ? 4 : 2);
+    bool aligned = (S % want == 0) && ((uintptr_t)r.A % (es * want) == 0) && ((uintptr_t)r.B % (es * want) == 0);
+    for (int k = 0; k < d; k++) aligned = aligned && (kp.lda[k] % want == 0) && (kp.ldb[k] % want == 0);
+    if (aligned && want > 1) vec = want;
+    L->vec = vec;
+    const int64_t per = 256LL * vec;
+    kp.nchunk = (S + per - 1) / per;
+    kp.cpb = (int)std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+    const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
+    kp.pre[0] = 0;
+    for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
+    for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+    if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
+  } else {
+    L->kernel = 1;
+    kp.gpre[0] = 0;
+    for (int p = 0; p < np; p++) kp.gpre[p + 1] = kp.gpre[p] + kp.norb[p] * S;
+    for (int p = np; p < 8; p++) kp.gpre[p + 1] = kp.gpre[p];
+    kp.ngroup = kp.gpre[np];
+    if ((kp.ngroup + 255) / 256 > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large");
+  }
+  return SPINSUM_OK;
+}
+
+int run(const Request& r, cudaStream_t st) {
+  t_err.clear();
+  Launch L;
+  int rc = plan_one(r, &L);
+  if (rc != SPINSUM_OK || L.empty) return rc;
+  cudaError_t e = L.kernel == 0 ? launch_k1(r.d, L.kp, L.ar, L.vec, st) : launch_kg(r.d, L.kp, L.ar, st);
+  t_launches++;
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return SPINSUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spinsum_3d(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
+               const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream) {
+  Request r{3, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run(r, (cudaStream_t)stream);
+}
+
+int spinsum_4d(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
+               const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream) {
+  Request r{4, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run(r, (cudaStream_t)stream);
+}
+
+int spinsum_check_status(spinsum_stream_t stream) {
+  t_err.clear();
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int st = 0;
+  e = read_and_clear_status(&st);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+  if (st == 1) return fail(SPINSUM_ERR_TIMEOUT, "a device-side bounded wait ran out");
+  if (st != 0) return fail(SPINSUM_ERR_DEVICE, "device status %d", st);
+  return SPINSUM_OK;
+}
+
+const char* spinsum_last_error(void) { return t_err.c_str(); }
+
+int64_t spinsum_launch_count(int reset) {
+  int64_t v = t_launches;
+  if (reset) t_launches = 0;
+  return v;
+}
+
+const char* spinsum_version(void) { return "spinsum-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batched plans (filled in by the batched work-list kernel)
+// ---------------------------------------------------------------------------
+struct spinsum_plan {
+  std::string desc;
+};
+
+extern "C" {
+
+int spinsum_plan_create(spinsum_plan** plan, const spinsum_problem* problems, int nproblems, int dtype,
+                        int allow_tuning_runs, spinsum_stream_t stream) {
+  (void)problems; (void)nproblems; (void)dtype; (void)allow_tuning_runs; (void)stream;
+  if (plan) *plan = nullptr;
+  return fail(SPINSUM_ERR_UNSUPPORTED, "batched plans are not built yet");
+}
+
+int spinsum_plan_execute(spinsum_plan* plan, spinsum_stream_t stream) {
+  (void)plan; (void)stream;
+  return fail(SPINSUM_ERR_UNSUPPORTED, "batched plans are not built yet");
+}
+
+int spinsum_plan_destroy(spinsum_plan* plan) {
+  delete plan;
+  return SPINSUM_OK;
+}
+
+const char* spinsum_plan_describe(const spinsum_plan* plan) { return plan ? plan->desc.c_str() : ""; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Planner introspection for host-side tests (not part of the public ABI):
+// plans a d-dimensional problem with permuted extent O and spectator extent V
+// (fake device addresses, nothing is launched) and reports the expanded
+// coefficients, the arithmetic choice and the launch shape.
+// info: [arith, W, kdrop, nstage, kernel, vec, flags, cexp, emin>>20, emax>>20,
+//        norb[0..7], blocks]
+// ---------------------------------------------------------------------------
+extern "C" int ss_debug_plan(int d, int O, int V, const double* coef, int nfactors, int mode, double alpha,
+                             double beta, double* expanded, int64_t* info, int* ci, int* mp) {
+  int64_t ext[8], ld[8];
+  int64_t s = 1;
+  for (int k = 0; k < 2 * d; k++) {
+    ext[k] = k < d ? V : O;
+    ld[k] = s;
+    s *= ext[k];
+  }
+  Request r{d, SPINSUM_F64, ext, (const void*)0x100000, ld, (void*)(0x100000 + 8 * s + 4096), ld,
+            coef, nfactors, mode, alpha, beta, 0};
+  Launch L;
+  int rc = plan_one(r, &L);
+  if (rc != SPINSUM_OK) return rc;
+  const Group& g = group(d);
+  std::vector<std::vector<double>> chain(nfactors, std::vector<double>(g.n));
+  for (int f = 0; f < nfactors; f++)
+    for (int x = 0; x < g.n; x++) chain[f][x] = coef[f * g.n + x];
+  std::vector<double> full = expand_chain(g, chain);
+  for (int x = 0; x < g.n; x++) expanded[x] = full[x];
+  const KParams& kp = L.kp;
+  int64_t v[32] = {L.ar, kp.W, kp.kdrop, kp.nstage, L.kernel, L.vec, kp.flags, kp.cexp, (int64_t)(kp.emin >> 20),
+                   (int64_t)(kp.emax >> 20)};
+  for (int p = 0; p < 8; p++) v[10 + p] = kp.norb[p];
+  v[18] = L.kernel == 0 ? kp.pre[npatterns(d)] : (kp.ngroup + 255) / 256;
+  for (int k = 0; k < 19; k++) info[k] = v[k];
+  for (int st = 0; st < MAXSTAGE; st++)
+    for (int x = 0; x < 24; x++) ci[st * 24 + x] = kp.ci[st][x];
+  for (int k = 0; k < MP_MAX; k++) mp[k] = kp.mp[k];
+  return SPINSUM_OK;
+}

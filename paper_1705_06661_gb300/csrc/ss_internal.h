@@ -1,0 +1,182 @@
+// Internal definitions shared by the host planner and the CUDA kernels of the
+// spin-summation library (not part of the public C-ABI).
+//
+// Orbits. For a canonical (sorted) permuted tuple t0 the tensor elements
+// A[s, t0 o tau], tau in S_d, form one orbit: the d! update statements of the
+// innermost loop of Algorithm 2 read and write exactly these elements, and
+// every A element is reused by all of them (Sec. 4.2). The members are the
+// distinct rearrangements of t0; their number m depends only on which entries
+// of t0 are equal (the "pattern"): {6, 3, 3, 1} for d = 3, and
+// {24, 12, 12, 12, 6, 4, 4, 1} for d = 4 (footnotes 3-4: equal-index cases
+// drop redundant updates). A pattern is given by a label tuple, e.g. (0,0,1)
+// for i = j < k; the orbits of a pattern are the strictly increasing choices
+// of its distinct values.
+//
+// Within an orbit, output member u of the summation needs input member
+// idx[u][sigma], the member equal to t_u o sigma (Def. 2), for every sigma in
+// lexicographic order. These tables are computed at compile time.
+#pragma once
+#include <stdint.h>
+
+namespace ss {
+
+constexpr int fact(int n) { return n <= 1 ? 1 : n * fact(n - 1); }
+constexpr int npatterns(int D) { return D == 2 ? 2 : (D == 3 ? 4 : 8); }
+
+// label tuple of pattern P (sorted, labels 0..nd-1)
+constexpr int pattern_label(int D, int P, int m) {
+  if (D == 2) {
+    constexpr int t[2][2] = {{0, 1}, {0, 0}};
+    return t[P][m];
+  }
+  if (D == 3) {
+    constexpr int t[4][3] = {{0, 1, 2}, {0, 0, 1}, {0, 1, 1}, {0, 0, 0}};
+    return t[P][m];
+  }
+  constexpr int t[8][4] = {{0, 1, 2, 3}, {0, 0, 1, 2}, {0, 1, 1, 2}, {0, 1, 2, 2},
+                           {0, 0, 1, 1}, {0, 0, 0, 1}, {0, 1, 1, 1}, {0, 0, 0, 0}};
+  return t[P][m];
+}
+
+template <int D>
+struct Sym {
+  int p[fact(D)][D] = {};
+};
+
+// S_D in lexicographic one-line order (0-based images), id first
+template <int D>
+constexpr Sym<D> make_sym() {
+  Sym<D> s{};
+  int a[D] = {};
+  for (int i = 0; i < D; i++) a[i] = i;
+  for (int n = 0; n < fact(D); n++) {
+    for (int i = 0; i < D; i++) s.p[n][i] = a[i];
+    int i = D - 2;
+    while (i >= 0 && a[i] > a[i + 1]) i--;
+    if (i < 0) break;
+    int j = D - 1;
+    while (a[j] < a[i]) j--;
+    int t = a[i]; a[i] = a[j]; a[j] = t;
+    for (int x = i + 1, y = D - 1; x < y; x++, y--) { t = a[x]; a[x] = a[y]; a[y] = t; }
+  }
+  return s;
+}
+
+template <int D>
+struct Pattern {
+  int m = 0;                    // orbit members
+  int nd = 0;                   // distinct values
+  int lab[fact(D)][D] = {};     // member label tuples, member 0 = canonical
+  int idx[fact(D)][fact(D)] = {};  // idx[u][sigma]: member equal to (member u) o sigma
+};
+
+template <int D>
+constexpr Pattern<D> make_pattern(int P) {
+  Pattern<D> r{};
+  Sym<D> S = make_sym<D>();
+  int base[D] = {};
+  int nd = 0;
+  for (int m = 0; m < D; m++) {
+    base[m] = pattern_label(D, P, m);
+    if (base[m] + 1 > nd) nd = base[m] + 1;
+  }
+  r.nd = nd;
+  // members: distinct base o tau, tau in lex order
+  for (int n = 0; n < fact(D); n++) {
+    int t[D] = {};
+    for (int m = 0; m < D; m++) t[m] = base[S.p[n][m]];
+    bool seen = false;
+    for (int u = 0; u < r.m; u++) {
+      bool same = true;
+      for (int m = 0; m < D; m++) same = same && r.lab[u][m] == t[m];
+      seen = seen || same;
+    }
+    if (!seen) {
+      for (int m = 0; m < D; m++) r.lab[r.m][m] = t[m];
+      r.m++;
+    }
+  }
+  for (int u = 0; u < r.m; u++) {
+    for (int n = 0; n < fact(D); n++) {
+      int t[D] = {};
+      for (int m = 0; m < D; m++) t[m] = r.lab[u][S.p[n][m]];
+      int v = -1;
+      for (int w = 0; w < r.m; w++) {
+        bool same = true;
+        for (int m = 0; m < D; m++) same = same && r.lab[w][m] == t[m];
+        if (same) v = w;
+      }
+      r.idx[u][n] = v;
+    }
+  }
+  return r;
+}
+
+template <int D, int P>
+struct PT {
+  static constexpr Pattern<D> t = make_pattern<D>(P);
+};
+
+// offsets of each pattern's dense expanded matrix in the M table
+template <int D>
+constexpr int mp_offset(int P) {
+  int o = 0;
+  for (int q = 1; q < P; q++) {
+    int m = make_pattern<D>(q).m;
+    o += m * m;
+  }
+  return o;
+}
+constexpr int MP_TOTAL_3 = 9 + 9 + 1;
+constexpr int MP_TOTAL_4 = 3 * 144 + 36 + 16 + 16 + 1;
+constexpr int MP_MAX = MP_TOTAL_4;
+
+constexpr int MAXSTAGE = 8;
+constexpr int MAXSTAGE_EXACT = 3;  // the exact core unrolls at most this many stages
+constexpr int MAXSPEC = 4;
+
+enum Arith { AR_EXACT = 0, AR_STRICT = 1, AR_F32 = 2 };
+
+// flags
+enum {
+  KF_BETA = 1,        // beta != 0: read B_old
+  KF_ALPHA_MUL = 2,   // exact path: alpha is not a power of two, multiply at the end
+  KF_KDROP = 4,       // exact path: round the fixed-point sum before conversion
+};
+
+// Kernel parameters (passed by value as a __grid_constant__).
+struct KParams {
+  const void* A;
+  void* B;
+  int64_t S;                    // spectator elements per permuted tuple
+  int64_t lda[4], ldb[4];       // permuted-index strides (elements)
+  // general spectator layout (used when the spectator block is not dense)
+  int64_t sext[MAXSPEC];        // spectator extents
+  int64_t slda[MAXSPEC], sldb[MAXSPEC];
+  int nspec;
+  int O;                        // permuted extent
+  int nstage;                   // stages of the FP64/FP32 sigma lists cd (1 = expanded)
+  int nci;                      // stages of the exact integer sigma lists ci (<= MAXSTAGE_EXACT)
+  int flags;
+  double alpha, beta;
+  // exact fixed-point path
+  int W;                        // limb width; grid = 2^(E+1-2W) of the orbit element's max
+  int s0;                       // 53 - 2W
+  int kdrop;                    // low bits rounded off the sum before conversion
+  long long rnd;                // 2^(kdrop-1) or 0
+  int cexp;                     // added to the max exponent field to build the conversion constant
+  unsigned emin, emax;          // fast path when the max exponent field lies in [emin, emax]
+  int ci[MAXSTAGE][24];         // sigma-list coefficients per stage, scaled integers (application order)
+  int mp[MP_MAX];               // degenerate patterns: expanded orbit matrices M_p, scaled integers
+  double cd[MAXSTAGE][24];      // sigma-list coefficients per stage (strict / FP32 path, application order)
+  // block mapping: pattern p owns blocks [pre[p], pre[p+1]); each block covers
+  // one orbit and cpb chunks of VEC*blockDim spectator elements
+  int64_t pre[9];
+  int64_t nchunk;               // chunks per orbit
+  int cpb;                      // chunks per block
+  int64_t norb[8];              // orbits per pattern
+  int64_t ngroup;               // general kernel: total orbit-element groups
+  int64_t gpre[9];              // general kernel: group prefix per pattern
+};
+
+}  // namespace ss

@@ -1,0 +1,449 @@
+#pragma once
+// CUDA kernel templates of the spin-summation library (sm_103a). Each
+// ss_k_*.cu translation unit instantiates a few of them, so the kernels
+// compile in parallel.
+//
+// K1 "orbit stream": the fast layout, where each permuted tuple owns a
+// contiguous run of S spectator elements. A CTA takes one orbit (the m <= d!
+// tuples t0 o tau of a canonical tuple t0, Sec. 4.2) and a range of spectator
+// positions; each thread loads the m member values at its position(s) with
+// coalesced vector loads, applies the m x m orbit operator in registers, and
+// stores the m results. Every element of A is read once and every element of
+// B written once (the temporal locality of Algorithm 2, at element level, with
+// the spatial locality of Sec. 4.6 coming from the spectator run instead of a
+// cache block). In place is safe: a thread reads all of its orbit positions
+// before it writes any, and no other thread touches them (Sec. 4.6.5).
+//
+// KG "general": one thread per (orbit, spectator position) with arbitrary
+// strides; used when the spectator block is not dense or too short.
+//
+// Arithmetic cores, per orbit element group x[0..m-1] -> y[0..m-1]:
+//   AR_EXACT  FP64 via exact fixed-point integer limbs (see exact_core)
+//   AR_STRICT FP64 natively, sigma in lexicographic order, multiply then add
+//   AR_F32    FP32 storage and accumulation
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ss_internal.h"
+
+namespace ss {
+
+template <int D, int P>
+struct Pat {
+  static constexpr int M = make_pattern<D>(P).m;
+  static constexpr int ND = make_pattern<D>(P).nd;
+  // table lookups; called with unrolled (compile-time) indices, so they fold to constants
+  __device__ __forceinline__ static int lab(int u, int k) {
+    constexpr Pattern<D> pt = make_pattern<D>(P);
+    return pt.lab[u][k];
+  }
+  __device__ __forceinline__ static int idx(int u, int s) {
+    constexpr Pattern<D> pt = make_pattern<D>(P);
+    return pt.idx[u][s];
+  }
+};
+
+// C(n, k) for k <= 4 with constant divisors (no 64-bit division routine);
+// k is a compile-time constant at every call site after unrolling
+__device__ __forceinline__ int64_t binom(int64_t n, int k) {
+  if (n < k) return 0;
+  switch (k) {
+    case 1: return n;
+    case 2: return n * (n - 1) / 2;
+    case 3: return n * (n - 1) * (n - 2) / 6;
+    case 4: return n * (n - 1) * (n - 2) * (n - 3) / 24;
+    default: return 1;
+  }
+}
+
+// strictly increasing ND-tuple of values in [0, O) with colex rank r
+// (combinatorial number system: r = sum_i C(v_i, i + 1))
+template <int ND>
+__device__ __forceinline__ void unrank(int64_t r, int O, int* v) {
+#pragma unroll
+  for (int i = ND - 1; i >= 0; i--) {
+    int c = i;
+    while (c + 1 < O && binom(c + 1, i + 1) <= r) c++;
+    v[i] = c;
+    r -= binom(c, i + 1);
+  }
+}
+
+__device__ __forceinline__ unsigned long long shr64(unsigned long long x, unsigned k) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(k));  // amounts >= 64 give 0
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// strict FP64 core: the reference order, stage by stage
+// ---------------------------------------------------------------------------
+template <int D, int P>
+__device__ __forceinline__ void strict_stage(const double* cd, double (&t)[Pat<D, P>::M]) {
+  constexpr int M = Pat<D, P>::M;
+  constexpr int NS = fact(D);
+  double acc[M];
+#pragma unroll
+  for (int u = 0; u < M; u++) acc[u] = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    const double c = cd[s];
+    if (c != 0.0) {
+#pragma unroll
+      for (int u = 0; u < M; u++) acc[u] = __dadd_rn(acc[u], __dmul_rn(c, t[Pat<D, P>::idx(u, s)]));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < M; u++) t[u] = acc[u];
+}
+
+template <int D, int P>
+__device__ __forceinline__ void strict_core(const KParams& kp, double (&t)[Pat<D, P>::M]) {
+  // the first three stages unrolled (coefficients become constant operands)
+#pragma unroll
+  for (int st = 0; st < 3; st++)
+    if (st < kp.nstage) strict_stage<D, P>(kp.cd[st], t);
+  for (int st = 3; st < kp.nstage; st++) strict_stage<D, P>(kp.cd[st], t);
+}
+
+// ---------------------------------------------------------------------------
+// exact FP64 core.
+// Let E be the largest biased exponent among the m inputs of the group. Every
+// input is truncated to the grid 2^(E-1022-2W) (two signed W-bit limbs, i.e.
+// 2W = 48..52 bits below the top of the largest input); the integer sums
+// sum_v M[u][v] X_v are exact in int32 per limb because sum|M[u][.]| * 2^W <
+// 2^31; the two limbs are joined into a 64-bit integer, rounded by kdrop bits
+// to below 2^51, and converted to FP64 exactly with one subtraction of a
+// magic constant C = 1.5 * 2^52 * ulp. Integer-valued inputs are therefore
+// reproduced exactly, and the error of any output is at most sum|a| * 2^(-2W)
+// times the largest input of its orbit plus 2^(kdrop-1) grid units.
+// Returns false (and leaves y untouched) when E is outside [emin, emax]:
+// zero or tiny groups, huge values, infinities and NaNs take the strict core.
+// ---------------------------------------------------------------------------
+template <int D, int P>
+__device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[Pat<D, P>::M],
+                                           double (&y)[Pat<D, P>::M]) {
+  constexpr int M = Pat<D, P>::M;
+  constexpr int NS = fact(D);
+  unsigned hi[M], lo[M];
+  unsigned E = 0;
+#pragma unroll
+  for (int v = 0; v < M; v++) {
+    hi[v] = (unsigned)__double2hiint(x[v]);
+    lo[v] = (unsigned)__double2loint(x[v]);
+    E = max(E, hi[v] & 0x7FF00000u);
+  }
+  if (E < kp.emin || E > kp.emax) return false;
+  const int W = kp.W;
+  const unsigned mask = (1u << W) - 1u;
+  int l0[M], l1[M];
+#pragma unroll
+  for (int v = 0; v < M; v++) {
+    unsigned k = ((E - (hi[v] & 0x7FF00000u)) >> 20) + (unsigned)kp.s0;
+    unsigned long long mant = ((unsigned long long)((hi[v] & 0x000FFFFFu) | 0x00100000u) << 32) | lo[v];
+    unsigned long long q = shr64(mant, k);
+    int a = (int)((unsigned)q & mask);
+    int b = (int)(q >> W);
+    int sg = (int)hi[v] >> 31;
+    l0[v] = (a ^ sg) - sg;
+    l1[v] = (b ^ sg) - sg;
+  }
+  int y0[M], y1[M];
+  if constexpr (P == 0) {
+#pragma unroll
+    for (int st = 0; st < MAXSTAGE_EXACT; st++) {
+      if (st >= kp.nci) break;
+#pragma unroll
+      for (int u = 0; u < M; u++) { y0[u] = 0; y1[u] = 0; }
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        const int c = kp.ci[st][s];
+        if (c != 0) {
+#pragma unroll
+          for (int u = 0; u < M; u++) {
+            y0[u] += c * l0[Pat<D, P>::idx(u, s)];
+            y1[u] += c * l1[Pat<D, P>::idx(u, s)];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < M; u++) { l0[u] = y0[u]; l1[u] = y1[u]; }
+    }
+  } else {
+    const int* mp = kp.mp + mp_offset<D>(P);
+#pragma unroll
+    for (int u = 0; u < M; u++) {
+      int a = 0, b = 0;
+#pragma unroll
+      for (int v = 0; v < M; v++) {
+        a += mp[u * M + v] * l0[v];
+        b += mp[u * M + v] * l1[v];
+      }
+      y0[u] = a;
+      y1[u] = b;
+    }
+#pragma unroll
+    for (int u = 0; u < M; u++) { l0[u] = y0[u]; l1[u] = y1[u]; }
+  }
+  const unsigned chi = E + (unsigned)kp.cexp;
+  const double C = __hiloint2double((int)chi, 0);
+#pragma unroll
+  for (int u = 0; u < M; u++) {
+    long long Y = ((long long)l1[u] << W) + (long long)l0[u];
+    if (kp.flags & KF_KDROP) Y = (Y + kp.rnd) >> kp.kdrop;
+    double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
+    y[u] = __dsub_rn(Dv, C);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// one orbit element group: x (inputs, m members) -> y (outputs), incl. alpha/beta
+// ---------------------------------------------------------------------------
+template <int D, int P, int AR, typename T>
+__device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>::M], T (&y)[Pat<D, P>::M]) {
+  constexpr int M = Pat<D, P>::M;
+  constexpr int NS = fact(D);
+  if constexpr (AR == AR_F32) {
+    float t[M];
+#pragma unroll
+    for (int u = 0; u < M; u++) t[u] = x[u];
+    auto stage = [&](const double* cd) {
+      float acc[M];
+#pragma unroll
+      for (int u = 0; u < M; u++) acc[u] = 0.f;
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        const float c = (float)cd[s];
+        if (c != 0.f) {
+#pragma unroll
+          for (int u = 0; u < M; u++) acc[u] = fmaf(c, t[Pat<D, P>::idx(u, s)], acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < M; u++) t[u] = acc[u];
+    };
+#pragma unroll
+    for (int st = 0; st < 3; st++)
+      if (st < kp.nstage) stage(kp.cd[st]);
+    for (int st = 3; st < kp.nstage; st++) stage(kp.cd[st]);
+    const float al = (float)kp.alpha;
+#pragma unroll
+    for (int u = 0; u < M; u++) y[u] = al * t[u];
+  } else {
+    bool done = false;
+    if constexpr (AR == AR_EXACT) {
+      done = exact_core<D, P>(kp, x, y);
+      if (done && (kp.flags & KF_ALPHA_MUL)) {
+#pragma unroll
+        for (int u = 0; u < M; u++) y[u] = __dmul_rn(kp.alpha, y[u]);
+      }
+    }
+    if (!done) {
+      strict_core<D, P>(kp, x);
+#pragma unroll
+      for (int u = 0; u < M; u++) y[u] = __dmul_rn(kp.alpha, x[u]);
+    }
+  }
+}
+
+// B = alpha S(A) + beta B_old: the beta term, in the reference order for FP64
+__device__ __forceinline__ double add_beta(double y, double b, double beta) { return __dadd_rn(y, __dmul_rn(beta, b)); }
+__device__ __forceinline__ float add_beta(float y, float b, float beta) { return fmaf(beta, b, y); }
+
+template <typename T, int VEC>
+struct VecT;
+template <>
+struct VecT<double, 1> { using t = double; };
+template <>
+struct VecT<double, 2> { using t = double2; };
+template <>
+struct VecT<float, 1> { using t = float; };
+template <>
+struct VecT<float, 2> { using t = float2; };
+template <>
+struct VecT<float, 4> { using t = float4; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void vload(const T* p, T (&v)[VEC]) {
+  using V = typename VecT<T, VEC>::t;
+  V w = *reinterpret_cast<const V*>(p);
+  const T* e = reinterpret_cast<const T*>(&w);
+#pragma unroll
+  for (int i = 0; i < VEC; i++) v[i] = e[i];
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void vstore(T* p, const T (&v)[VEC]) {
+  using V = typename VecT<T, VEC>::t;
+  V w;
+  T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+  for (int i = 0; i < VEC; i++) e[i] = v[i];
+  *reinterpret_cast<V*>(p) = w;
+}
+
+// ---------------------------------------------------------------------------
+// K1 body for pattern P. Warp 0 unranks the orbit and writes the m member
+// offsets of A and B to shared memory; the CTA then streams cpb chunks of
+// VEC * blockDim spectator positions through registers.
+// ---------------------------------------------------------------------------
+template <int D, int P, int AR, int VEC, typename T>
+__device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t c0, int64_t c1) {
+  constexpr int M = Pat<D, P>::M;
+  __shared__ int64_t soff[2][24];
+  if (threadIdx.x < 32) {
+    int val[4] = {0, 0, 0, 0};
+    unrank<Pat<D, P>::ND>(orb, kp.O, val);
+#pragma unroll
+    for (int u = 0; u < M; u++) {
+      if (threadIdx.x == (u & 31)) {
+        int64_t a = 0, b = 0;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          const int t = val[Pat<D, P>::lab(u, k)];
+          a += (int64_t)t * kp.lda[k];
+          b += (int64_t)t * kp.ldb[k];
+        }
+        soff[0][u] = a;
+        soff[1][u] = b;
+      }
+    }
+  }
+  __syncthreads();
+  const T* A = static_cast<const T*>(kp.A);
+  T* B = static_cast<T*>(kp.B);
+  const int64_t step = (int64_t)blockDim.x * VEC;
+  for (int64_t c = c0; c < c1; c++) {
+    const int64_t s = c * step + (int64_t)threadIdx.x * VEC;
+    if (s >= kp.S) break;
+    T x[VEC][M], y[VEC][M];
+#pragma unroll
+    for (int u = 0; u < M; u++) {
+      T v[VEC];
+      vload<T, VEC>(A + soff[0][u] + s, v);
+#pragma unroll
+      for (int e = 0; e < VEC; e++) x[e][u] = v[e];
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T>(kp, x[e], y[e]);
+    const bool beta = kp.flags & KF_BETA;
+    const T bt = (T)kp.beta;
+#pragma unroll
+    for (int u = 0; u < M; u++) {
+      T v[VEC];
+      T* dst = B + soff[1][u] + s;
+      if (beta) {
+        vload<T, VEC>(dst, v);
+#pragma unroll
+        for (int e = 0; e < VEC; e++) v[e] = add_beta(y[e][u], v[e], bt);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; e++) v[e] = y[e][u];
+      }
+      vstore<T, VEC>(dst, v);
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ int find_pattern(const int64_t* pre, int64_t b) {
+  int p = 0;
+#pragma unroll
+  for (int q = 1; q < npatterns(D); q++)
+    if (b >= pre[q]) p = q;
+  return p;
+}
+
+template <int D, int AR, int VEC, typename T>
+__global__ void __launch_bounds__(256) k1_kernel(const __grid_constant__ KParams kp) {
+  const int64_t b = blockIdx.x;
+  const int p = find_pattern<D>(kp.pre, b);
+  const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;  // blocks per orbit
+  const int64_t local = b - kp.pre[p];
+  const int64_t orb = local / bpo;
+  const int64_t cb = local - orb * bpo;
+  const int64_t c0 = cb * kp.cpb;
+  const int64_t c1 = min(kp.nchunk, c0 + kp.cpb);
+  switch (p) {
+    case 0: k1_body<D, 0, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 1: k1_body<D, 1, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 2: k1_body<D, 2, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 3: k1_body<D, 3, AR, VEC, T>(kp, orb, c0, c1); break;
+    default:
+      if constexpr (D == 4) {
+        switch (p) {
+          case 4: k1_body<D, 4, AR, VEC, T>(kp, orb, c0, c1); break;
+          case 5: k1_body<D, 5, AR, VEC, T>(kp, orb, c0, c1); break;
+          case 6: k1_body<D, 6, AR, VEC, T>(kp, orb, c0, c1); break;
+          case 7: k1_body<D, 7, AR, VEC, T>(kp, orb, c0, c1); break;
+        }
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// KG: general strides, one thread per orbit element group
+// ---------------------------------------------------------------------------
+template <int D, int P, int AR, typename T>
+__device__ __forceinline__ void kg_body(const KParams& kp, int64_t g) {
+  constexpr int M = Pat<D, P>::M;
+  const int64_t orb = g / kp.S;
+  int64_t s = g - orb * kp.S;
+  int64_t sa = 0, sb = 0;
+  for (int k = 0; k < kp.nspec; k++) {
+    const int64_t q = s / kp.sext[k];
+    const int64_t r = s - q * kp.sext[k];
+    sa += r * kp.slda[k];
+    sb += r * kp.sldb[k];
+    s = q;
+  }
+  int val[4] = {0, 0, 0, 0};
+  unrank<Pat<D, P>::ND>(orb, kp.O, val);
+  const T* A = static_cast<const T*>(kp.A);
+  T* B = static_cast<T*>(kp.B);
+  int64_t offA[M], offB[M];
+#pragma unroll
+  for (int u = 0; u < M; u++) {
+    int64_t a = sa, b = sb;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      const int t = val[Pat<D, P>::lab(u, k)];
+      a += (int64_t)t * kp.lda[k];
+      b += (int64_t)t * kp.ldb[k];
+    }
+    offA[u] = a;
+    offB[u] = b;
+  }
+  T x[M], y[M];
+#pragma unroll
+  for (int u = 0; u < M; u++) x[u] = A[offA[u]];
+  apply_group<D, P, AR, T>(kp, x, y);
+  const T bt = (T)kp.beta;
+#pragma unroll
+  for (int u = 0; u < M; u++) B[offB[u]] = (kp.flags & KF_BETA) ? add_beta(y[u], B[offB[u]], bt) : y[u];
+}
+
+template <int D, int AR, typename T>
+__global__ void __launch_bounds__(256) kg_kernel(const __grid_constant__ KParams kp) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= kp.ngroup) return;
+  const int p = find_pattern<D>(kp.gpre, g);
+  const int64_t lg = g - kp.gpre[p];
+  switch (p) {
+    case 0: kg_body<D, 0, AR, T>(kp, lg); break;
+    case 1: kg_body<D, 1, AR, T>(kp, lg); break;
+    case 2: kg_body<D, 2, AR, T>(kp, lg); break;
+    case 3: kg_body<D, 3, AR, T>(kp, lg); break;
+    default:
+      if constexpr (D == 4) {
+        switch (p) {
+          case 4: kg_body<D, 4, AR, T>(kp, lg); break;
+          case 5: kg_body<D, 5, AR, T>(kp, lg); break;
+          case 6: kg_body<D, 6, AR, T>(kp, lg); break;
+          case 7: kg_body<D, 7, AR, T>(kp, lg); break;
+        }
+      }
+  }
+}
+
+}  // namespace ss
