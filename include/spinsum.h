@@ -65,8 +65,12 @@ enum spinsum_mode {
   SPINSUM_EXPANDED = 0,   /* multiply the chain out on the host (product rule), one pass of d!-term sums */
   SPINSUM_FACTORIZED = 1, /* apply the factors stage by stage on chip, innermost first (Def. 4) */
   SPINSUM_ADJOINT = 2,    /* apply the transpose S^T = F_k^T ... F_1^T, F^T(sigma) = F(sigma^-1) */
-  SPINSUM_STRICT = 4      /* FP64 only: native FP64 arithmetic in the reference order (lex sigma,
+  SPINSUM_STRICT = 4,     /* FP64 only: native FP64 arithmetic in the reference order (lex sigma,
                              multiply then add, no FMA), bit-identical to a plain loop nest */
+  SPINSUM_TMA = 8         /* 3D, exact FP64 or FP32: stage orbits through shared memory with TMA bulk
+                             copies (producer warp + mbarrier ring) instead of the default
+                             register-streaming kernel; same results. Ignored where it does not apply
+                             (4D, strict, unaligned or odd spectator blocks) and in batched plans. */
 };
 
 /*

@@ -29,6 +29,7 @@ SPINSUM_EXPANDED = 0
 SPINSUM_FACTORIZED = 1
 SPINSUM_ADJOINT = 2
 SPINSUM_STRICT = 4
+SPINSUM_TMA = 8
 
 _STATUS_NAMES = {
     -1: "SPINSUM_ERR_ARG", -2: "SPINSUM_ERR_ALIAS", -3: "SPINSUM_ERR_UNSUPPORTED", -4: "SPINSUM_ERR_CUDA",

@@ -53,8 +53,9 @@ def _dims(x: torch.Tensor, d: int):
 
 
 def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | None = None,
-            factorized: bool = False, adjoint: bool = False, strict: bool = False, alpha: float = 1.0,
-            beta: float = 0.0, inplace: bool = False, stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+            factorized: bool = False, adjoint: bool = False, strict: bool = False, tma: bool = False,
+            alpha: float = 1.0, beta: float = 0.0, inplace: bool = False,
+            stream: torch.cuda.Stream | None = None) -> torch.Tensor:
     """B = alpha * S(A) + beta * B (or A in place), S the spin summation of the
     coefficient chain `coef` ([nfactors, d!], lexicographic permutation order)."""
     if d is None:
@@ -81,7 +82,7 @@ def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | 
     ext, lda = _dims(A, d)
     _, ldb = _dims(out, d)
     mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
-        | (_b.SPINSUM_STRICT if strict else 0)
+        | (_b.SPINSUM_STRICT if strict else 0) | (_b.SPINSUM_TMA if tma else 0)
     st = (stream or torch.cuda.current_stream(A.device)).cuda_stream
     fn = _b.spinsum_3d if d == 3 else _b.spinsum_4d
     with torch.cuda.device(A.device):
@@ -110,3 +111,69 @@ def spinsum_autograd(A: torch.Tensor, coef, *, d: int | None = None, factorized:
                      alpha: float = 1.0) -> torch.Tensor:
     d = d if d is not None else A.dim() // 2
     return SpinSumFunction.apply(A, _coef_chain(coef, d), d, factorized, float(alpha))
+
+
+class Plan:
+    """Batched spin summations run by one persistent kernel launch per
+    (d, arithmetic) class (spinsum_plan_create / _execute / _destroy).
+
+    problems: list of dicts with keys A, coef and optionally B (output; None
+    means in place), d, factorized, adjoint, strict, alpha, beta. All tensors
+    share one dtype. tune=True lets the autotuner time candidate tilings
+    (which runs the problems); tune=False uses the heuristic."""
+
+    def __init__(self, problems, tune: bool = True, stream: torch.cuda.Stream | None = None):
+        self._keep = []
+        structs = []
+        dtypes = set()
+        for p in problems:
+            A = p["A"]
+            d = p.get("d", A.dim() // 2)
+            B = p.get("B")
+            inplace = B is None
+            out = A if inplace else B
+            c = _coef_chain(p["coef"], d)
+            ext, lda = _dims(A, d)
+            _, ldb = _dims(out, d)
+            mode = (_b.SPINSUM_FACTORIZED if p.get("factorized") else 0) | (
+                _b.SPINSUM_ADJOINT if p.get("adjoint") else 0) | (_b.SPINSUM_STRICT if p.get("strict") else 0)
+            s = _b.spinsum_problem()
+            s.d = d
+            for k in range(2 * d):
+                s.ext[k], s.lda[k], s.ldb[k] = int(ext[k]), int(lda[k]), int(ldb[k])
+            s.A, s.B = A.data_ptr(), out.data_ptr()
+            s.coef = c.ctypes.data
+            s.nfactors = c.shape[0]
+            s.mode = mode
+            s.alpha, s.beta = float(p.get("alpha", 1.0)), float(p.get("beta", 0.0))
+            s.inplace = int(inplace)
+            structs.append(s)
+            self._keep += [A, out, c]
+            dtypes.add(A.dtype)
+        if len(dtypes) > 1:
+            raise ValueError("all problems of a plan share one dtype")
+        dt = dtypes.pop() if dtypes else torch.float64
+        self.dtype = _b.SPINSUM_F64 if dt == torch.float64 else _b.SPINSUM_F32
+        dev = problems[0]["A"].device if problems else torch.device("cuda")
+        st = (stream or torch.cuda.current_stream(dev)).cuda_stream
+        with torch.cuda.device(dev):
+            self._h = _b.spinsum_plan_create(structs, self.dtype, int(tune), st)
+        self.device = dev
+
+    def execute(self, stream: torch.cuda.Stream | None = None) -> None:
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        _b.spinsum_plan_execute(self._h, st)
+
+    def describe(self) -> str:
+        return _b.spinsum_plan_describe(self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _b.spinsum_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,6 +6,8 @@
 #include <atomic>
 #include <cstdarg>
 #include <algorithm>
+#include <array>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +20,10 @@
 namespace ss {
 cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st);
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st);
+int k1t_chunk(int d, int ar);
+
+int* status_ptr();
 cudaError_t read_and_clear_status(int* out);
 }  // namespace ss
 
@@ -164,6 +170,17 @@ void fill_mp(const std::vector<long long>& a, int* mp) {
   }
 }
 
+// polls of a bounded device-side wait before it reports SPINSUM_ERR_TIMEOUT;
+// SPINSUM_WAIT_LIMIT overrides the default (2^22 polls, well under a minute)
+long long wait_limit() {
+  static long long v = [] {
+    const char* e = getenv("SPINSUM_WAIT_LIMIT");
+    long long x = e ? atoll(e) : 0;
+    return x > 0 ? x : (1LL << 22);
+  }();
+  return v;
+}
+
 struct Request {
   int d, dtype;
   const int64_t* ext;
@@ -186,19 +203,11 @@ void span(int n, const int64_t* ext, const int64_t* ld, const void* base, size_t
   *hi = (uintptr_t)base + (uintptr_t)((mx + 1) * (int64_t)es);
 }
 
-struct Launch {
-  KParams kp;
-  int ar = AR_STRICT;
-  int kernel = 0;  // 0 = K1, 1 = KG
-  int vec = 1;
-  bool empty = false;
-};
-
 int plan_one(const Request& r, Launch* L) {
   const int d = r.d;
   if (d != 3 && d != 4) return fail(SPINSUM_ERR_ARG, "d must be 3 or 4");
   if (r.dtype != SPINSUM_F64 && r.dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", r.dtype);
-  if (r.mode & ~(SPINSUM_FACTORIZED | SPINSUM_ADJOINT | SPINSUM_STRICT))
+  if (r.mode & ~(SPINSUM_FACTORIZED | SPINSUM_ADJOINT | SPINSUM_STRICT | SPINSUM_TMA))
     return fail(SPINSUM_ERR_ARG, "unknown mode bits 0x%x", r.mode);
   if ((r.mode & SPINSUM_STRICT) && r.dtype != SPINSUM_F64)
     return fail(SPINSUM_ERR_ARG, "SPINSUM_STRICT applies to FP64 only");
@@ -266,7 +275,13 @@ int plan_one(const Request& r, Launch* L) {
   kp.nstage = (int)stages.size();
   kp.flags = r.beta != 0.0 ? KF_BETA : 0;
   for (int st = 0; st < kp.nstage; st++)
-    for (int s = 0; s < g.n; s++) kp.cd[st][s] = stages[st][s];
+    for (int s = 0; s < g.n; s++) {
+      kp.cd[st][s] = stages[st][s];
+      kp.cf[st][s] = (float)stages[st][s];
+    }
+  kp.alphaf = (float)r.alpha;
+  kp.betaf = (float)r.beta;
+  kp.wait_limit = wait_limit();
   for (int k = 0; k < d; k++) {
     kp.lda[k] = r.lda[d + k];
     kp.ldb[k] = r.ldb[d + k];
@@ -369,18 +384,33 @@ int plan_one(const Request& r, Launch* L) {
   if (dense && S >= 64) {
     L->kernel = 0;
     int vec = 1;
-    const int want = (r.dtype == SPINSUM_F64) ? (d == 3 ? 2 : 1) : (d == 3 ? 4 : 2);
+    const int want = d == 3 ? (r.dtype == SPINSUM_F64 ? 2 : 4) : 1;
     bool aligned = (S % want == 0) && ((uintptr_t)r.A % (es * want) == 0) && ((uintptr_t)r.B % (es * want) == 0);
     for (int k = 0; k < d; k++) aligned = aligned && (kp.lda[k] % want == 0) && (kp.ldb[k] % want == 0);
     if (aligned && want > 1) vec = want;
     L->vec = vec;
-    const int64_t per = 256LL * vec;
-    kp.nchunk = (S + per - 1) / per;
-    kp.cpb = (int)std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
-    const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
-    kp.pre[0] = 0;
-    for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
-    for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+    // TMA staging: every member run must start on a 16-byte boundary and span a
+    // multiple of 16 bytes (bulk-copy rule), and the vector width must divide S
+    bool tma = (r.mode & SPINSUM_TMA) && d == 3 && L->ar != AR_STRICT && aligned && (S * (int64_t)es) % 16 == 0 &&
+               (uintptr_t)r.A % 16 == 0 && (uintptr_t)r.B % 16 == 0;
+    for (int k = 0; k < d; k++) tma = tma && (kp.lda[k] * (int64_t)es) % 16 == 0;
+    if (tma) {
+      L->kernel = 2;
+      const int ch = k1t_chunk(d, L->ar);
+      kp.nchunk = (S + ch - 1) / ch;
+      kp.cpb = 1;
+      kp.pre[0] = 0;
+      for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * kp.nchunk;
+      for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+    } else {
+      const int64_t per = 256LL * vec;
+      kp.nchunk = (S + per - 1) / per;
+      kp.cpb = (int)std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+      const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
+      kp.pre[0] = 0;
+      for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
+      for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+    }
     if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
   } else {
     L->kernel = 1;
@@ -398,7 +428,10 @@ int run(const Request& r, cudaStream_t st) {
   Launch L;
   int rc = plan_one(r, &L);
   if (rc != SPINSUM_OK || L.empty) return rc;
-  cudaError_t e = L.kernel == 0 ? launch_k1(r.d, L.kp, L.ar, L.vec, st) : launch_kg(r.d, L.kp, L.ar, st);
+  L.kp.status = status_ptr();
+  cudaError_t e = L.kernel == 0   ? launch_k1(r.d, L.kp, L.ar, L.vec, st)
+                  : L.kernel == 2 ? launch_k1t(r.d, L.kp, L.ar, st)
+                                  : launch_kg(r.d, L.kp, L.ar, st);
   t_launches++;
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return SPINSUM_OK;
@@ -447,27 +480,309 @@ const char* spinsum_version(void) { return "spinsum-gb300 0.1 (sm_103a)"; }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// batched plans (filled in by the batched work-list kernel)
+// batched plans: problems grouped by (d, arithmetic); each class runs as one
+// persistent launch of the batched kernel over its problems' K1 blocks.
+// Problems whose layout needs the general kernel are launched one by one.
 // ---------------------------------------------------------------------------
+namespace ss {
+cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                      cudaStream_t st, const void** fn);
+}
+
+namespace {
+
+// K1 blocks of one problem for a given number of chunks per block
+void set_cpb(KParams& kp, int d, int cpb) {
+  kp.cpb = (int)std::max<int64_t>(1, std::min<int64_t>(cpb, kp.nchunk));
+  const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
+  const int np = npatterns(d);
+  kp.pre[0] = 0;
+  for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
+  for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+}
+
+// a batch image in host memory (same layout as the device copy)
+struct BatchLayout {
+  KParams* probs;
+  int64_t* prefix;
+  int* vec;
+};
+
+struct ClassRange {
+  int d, ar, first, pfirst, n;
+  int64_t blocks;
+};
+
+// bytes and field offsets of an image for n problems
+struct ImageShape {
+  size_t probs, prefix, vec, bytes;
+};
+ImageShape image_shape(int n) {
+  ImageShape sh;
+  sh.probs = 0;
+  sh.prefix = sizeof(KParams) * (size_t)n;
+  sh.vec = sh.prefix + sizeof(int64_t) * (size_t)(n + 8);
+  sh.bytes = sh.vec + sizeof(int) * (size_t)n;
+  return sh;
+}
+
+// Fill the image with the K1-capable launches in the given order, grouped by
+// class, each with K1 chunking and `cpb` chunks per block (cpb <= 0: the
+// single-call heuristic of 8192 positions per block).
+std::vector<ClassRange> fill_batch(const std::vector<Launch>& ls, const std::vector<int>& order, int cpb,
+                                   BatchLayout out, int* status) {
+  std::vector<ClassRange> cls;
+  int next = 0, pnext = 0;
+  for (int d : {3, 4})
+    for (int ar : {(int)AR_EXACT, (int)AR_STRICT, (int)AR_F32}) {
+      ClassRange c{d, ar, next, pnext, 0, 0};
+      for (int i : order) {
+        const Launch& L = ls[i];
+        if (L.kernel == 1 || L.kp.nspec != d || L.ar != ar) continue;
+        KParams kp = L.kp;
+        kp.status = status;
+        const int vec = (L.vec > 1 && !(d == 4 && L.ar == AR_F32)) ? L.vec : 1;
+        kp.nchunk = (kp.S + 256LL * vec - 1) / (256LL * vec);
+        set_cpb(kp, d, cpb > 0 ? cpb : (int)std::max<int64_t>(1, 8192 / (256LL * vec)));
+        out.probs[next] = kp;
+        out.vec[next] = vec;
+        out.prefix[pnext + c.n] = c.blocks;
+        c.blocks += kp.pre[npatterns(d)];
+        next++;
+        c.n++;
+      }
+      if (c.n == 0) continue;
+      out.prefix[pnext + c.n] = c.blocks;
+      pnext += c.n + 1;
+      cls.push_back(c);
+    }
+  return cls;
+}
+
+int64_t problem_bytes(const Launch& L) {
+  int64_t n = L.kp.S;
+  for (int k = 0; k < L.kp.nspec; k++) n *= L.kp.O;
+  return n;
+}
+
+}  // namespace
+
 struct spinsum_plan {
+  int device = 0;
+  int dtype = SPINSUM_F64;
+  std::vector<Launch> launches;      // one per non-empty problem
+  std::vector<int> general;          // problems run by the general kernel
+  std::vector<ClassRange> classes;
+  std::vector<int> grid;             // per class
+  unsigned char* d_image = nullptr;  // device copy of the batch image (owned)
+  ImageShape shape{};
+  int cpb_scale = 3;                 // chunks per block = 2^cpb_scale
+  int order = 0;                     // 0 as given, 1 largest problems first
+  int occ = 1;                       // grid = SMs * max blocks per SM / occ
   std::string desc;
 };
+
+namespace {
+
+int plan_build(spinsum_plan* P, int cpb_scale, int order, int occ, cudaStream_t st) {
+  const int n = (int)P->launches.size();
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; i++) idx[i] = i;
+  if (order == 1)
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return problem_bytes(P->launches[a]) > problem_bytes(P->launches[b]); });
+  std::vector<unsigned char> img(P->shape.bytes, 0);
+  BatchLayout lay{reinterpret_cast<KParams*>(img.data() + P->shape.probs),
+                  reinterpret_cast<int64_t*>(img.data() + P->shape.prefix),
+                  reinterpret_cast<int*>(img.data() + P->shape.vec)};
+  P->classes = fill_batch(P->launches, idx, 1 << cpb_scale, lay, status_ptr());
+  cudaError_t e = cudaMemcpyAsync(P->d_image, img.data(), img.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the plan");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  P->grid.clear();
+  for (const ClassRange& c : P->classes) {
+    const void* fn = nullptr;
+    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, 0, st, &fn);
+    int nb = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int64_t full = (int64_t)sms * std::max(1, nb) / occ;
+    P->grid.push_back((int)std::max<int64_t>(1, std::min<int64_t>(c.blocks, full)));
+  }
+  P->cpb_scale = cpb_scale;
+  P->order = order;
+  P->occ = occ;
+  return SPINSUM_OK;
+}
+
+int plan_launch(spinsum_plan* P, cudaStream_t st) {
+  const KParams* probs = reinterpret_cast<const KParams*>(P->d_image + P->shape.probs);
+  const int64_t* prefix = reinterpret_cast<const int64_t*>(P->d_image + P->shape.prefix);
+  const int* vec = reinterpret_cast<const int*>(P->d_image + P->shape.vec);
+  for (size_t k = 0; k < P->classes.size(); k++) {
+    const ClassRange& c = P->classes[k];
+    cudaError_t e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, P->grid[k], st,
+                              nullptr);
+    t_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
+  }
+  for (int i : P->general) {
+    Launch L = P->launches[i];
+    L.kp.status = status_ptr();
+    cudaError_t e = launch_kg(L.kp.nspec, L.kp, L.ar, st);
+    t_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "general kernel launch");
+  }
+  return SPINSUM_OK;
+}
+
+// autotune cache: key -> (cpb_scale, order, occ); kept for the process, and
+// in the file named by SPINSUM_AUTOTUNE_CACHE when set
+std::string tune_key(const spinsum_plan* P) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, P->device);
+  std::string k = std::string(prop.name) + "|dt" + std::to_string(P->dtype);
+  for (const Launch& L : P->launches) {
+    char buf[96];
+    snprintf(buf, sizeof buf, "|%d:%lld:%d:%d:%d", L.kp.nspec, (long long)L.kp.S, L.kp.O, L.ar, L.vec);
+    k += buf;
+  }
+  return k;
+}
+
+std::vector<std::pair<std::string, std::array<int, 3>>>& tune_cache() {
+  static std::vector<std::pair<std::string, std::array<int, 3>>> c;
+  static bool loaded = false;
+  if (!loaded) {
+    loaded = true;
+    if (const char* f = getenv("SPINSUM_AUTOTUNE_CACHE")) {
+      if (FILE* fp = fopen(f, "r")) {
+        char line[8192];
+        while (fgets(line, sizeof line, fp)) {
+          char* tab = strrchr(line, '\t');
+          if (!tab) continue;
+          *tab = 0;
+          int a, b, cc;
+          if (sscanf(tab + 1, "%d %d %d", &a, &b, &cc) == 3) c.push_back({line, {a, b, cc}});
+        }
+        fclose(fp);
+      }
+    }
+  }
+  return c;
+}
+
+void tune_store(const std::string& key, int a, int b, int c) {
+  tune_cache().push_back({key, {a, b, c}});
+  if (const char* f = getenv("SPINSUM_AUTOTUNE_CACHE")) {
+    if (FILE* fp = fopen(f, "a")) {
+      fprintf(fp, "%s\t%d %d %d\n", key.c_str(), a, b, c);
+      fclose(fp);
+    }
+  }
+}
+
+void plan_free(spinsum_plan* P) {
+  if (P->d_image) cudaFree(P->d_image);
+  P->d_image = nullptr;
+}
+
+}  // namespace
 
 extern "C" {
 
 int spinsum_plan_create(spinsum_plan** plan, const spinsum_problem* problems, int nproblems, int dtype,
                         int allow_tuning_runs, spinsum_stream_t stream) {
-  (void)problems; (void)nproblems; (void)dtype; (void)allow_tuning_runs; (void)stream;
-  if (plan) *plan = nullptr;
-  return fail(SPINSUM_ERR_UNSUPPORTED, "batched plans are not built yet");
+  t_err.clear();
+  if (!plan) return fail(SPINSUM_ERR_ARG, "null plan pointer");
+  *plan = nullptr;
+  if (nproblems < 0 || (nproblems > 0 && !problems)) return fail(SPINSUM_ERR_ARG, "bad problem list");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* P = new spinsum_plan();
+  P->dtype = dtype;
+  cudaError_t e = cudaGetDevice(&P->device);
+  if (e != cudaSuccess) { delete P; return cuda_fail(e, "cudaGetDevice"); }
+  for (int i = 0; i < nproblems; i++) {
+    const spinsum_problem& q = problems[i];
+    Request r{q.d, dtype, q.ext, q.A, q.lda, q.B, q.ldb, q.coef, q.nfactors, q.mode & ~SPINSUM_TMA, q.alpha,
+              q.beta, q.inplace};
+    Launch L;
+    int rc = plan_one(r, &L);
+    if (rc != SPINSUM_OK) {
+      std::string m = "problem " + std::to_string(i) + ": " + t_err;
+      delete P;
+      return fail(rc, "%s", m.c_str());
+    }
+    if (L.empty) continue;
+    if (L.kernel == 1) P->general.push_back((int)P->launches.size());
+    P->launches.push_back(L);
+  }
+  P->shape = image_shape((int)P->launches.size());
+  e = cudaMalloc(&P->d_image, std::max<size_t>(P->shape.bytes, 16));
+  if (e != cudaSuccess) { delete P; return cuda_fail(e, "allocating the plan image"); }
+  int best[3] = {3, 0, 1};
+  const std::string key = tune_key(P);
+  bool cached = false;
+  for (auto& kv : tune_cache())
+    if (kv.first == key) {
+      best[0] = kv.second[0]; best[1] = kv.second[1]; best[2] = kv.second[2];
+      cached = true;
+    }
+  const bool any_k1 = P->general.size() < P->launches.size();
+  if (!cached && allow_tuning_runs && any_k1) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int cs = 0; cs <= 5; cs++)
+      for (int order = 0; order <= 1; order++)
+        for (int occ = 1; occ <= 2; occ++) {
+          int rc = plan_build(P, cs, order, occ, st);
+          if (rc != SPINSUM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); plan_free(P); delete P; return rc; }
+          float ms = 1e30f;
+          for (int rep = 0; rep < 3; rep++) {
+            cudaEventRecord(e0, st);
+            rc = plan_launch(P, st);
+            cudaEventRecord(e1, st);
+            if (rc != SPINSUM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); plan_free(P); delete P; return rc; }
+            cudaEventSynchronize(e1);
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);
+          }
+          if (ms < best_ms) { best_ms = ms; best[0] = cs; best[1] = order; best[2] = occ; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, best[0], best[1], best[2]);
+  }
+  int rc = plan_build(P, best[0], best[1], best[2], st);
+  if (rc != SPINSUM_OK) { plan_free(P); delete P; return rc; }
+  char buf[256];
+  int64_t blocks = 0;
+  for (auto& c : P->classes) blocks += c.blocks;
+  snprintf(buf, sizeof buf,
+           "problems=%zu classes=%zu general=%zu blocks=%lld chunks_per_block=%d order=%s occupancy=1/%d%s",
+           P->launches.size(), P->classes.size(), P->general.size(), (long long)blocks, 1 << best[0],
+           best[1] ? "largest-first" : "as-given", best[2],
+           cached ? " (cached)" : (allow_tuning_runs ? " (tuned)" : " (heuristic)"));
+  P->desc = buf;
+  *plan = P;
+  return SPINSUM_OK;
 }
 
 int spinsum_plan_execute(spinsum_plan* plan, spinsum_stream_t stream) {
-  (void)plan; (void)stream;
-  return fail(SPINSUM_ERR_UNSUPPORTED, "batched plans are not built yet");
+  t_err.clear();
+  if (!plan) return fail(SPINSUM_ERR_ARG, "null plan");
+  return plan_launch(plan, (cudaStream_t)stream);
 }
 
 int spinsum_plan_destroy(spinsum_plan* plan) {
+  t_err.clear();
+  if (!plan) return SPINSUM_OK;
+  plan_free(plan);
   delete plan;
   return SPINSUM_OK;
 }

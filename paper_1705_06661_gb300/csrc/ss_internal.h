@@ -131,6 +131,20 @@ constexpr int MP_TOTAL_3 = 9 + 9 + 1;
 constexpr int MP_TOTAL_4 = 3 * 144 + 36 + 16 + 16 + 1;
 constexpr int MP_MAX = MP_TOTAL_4;
 
+// K1T pipeline shape: consumer warps and stages per CTA (3D / 4D)
+#ifndef SS_K1T3_NCW
+#define SS_K1T3_NCW 8
+#endif
+#ifndef SS_K1T3_NST
+#define SS_K1T3_NST 4
+#endif
+#ifndef SS_K1T4_NCW
+#define SS_K1T4_NCW 8
+#endif
+#ifndef SS_K1T4_NST
+#define SS_K1T4_NST 3
+#endif
+
 constexpr int MAXSTAGE = 8;
 constexpr int MAXSTAGE_EXACT = 3;  // the exact core unrolls at most this many stages
 constexpr int MAXSPEC = 4;
@@ -144,8 +158,9 @@ enum {
   KF_KDROP = 4,       // exact path: round the fixed-point sum before conversion
 };
 
-// Kernel parameters (passed by value as a __grid_constant__).
-struct KParams {
+// Kernel parameters (passed by value as a __grid_constant__, or from a
+// device array in batched plans; 16-byte aligned so CTAs copy it as int4).
+struct alignas(16) KParams {
   const void* A;
   void* B;
   int64_t S;                    // spectator elements per permuted tuple
@@ -168,7 +183,11 @@ struct KParams {
   unsigned emin, emax;          // fast path when the max exponent field lies in [emin, emax]
   int ci[MAXSTAGE][24];         // sigma-list coefficients per stage, scaled integers (application order)
   int mp[MP_MAX];               // degenerate patterns: expanded orbit matrices M_p, scaled integers
-  double cd[MAXSTAGE][24];      // sigma-list coefficients per stage (strict / FP32 path, application order)
+  double cd[MAXSTAGE][24];      // sigma-list coefficients per stage (strict path, application order)
+  float cf[MAXSTAGE][24];       // the same rounded to FP32 (FP32 path)
+  float alphaf, betaf;
+  int* status;                  // device status word (bounded waits report here)
+  long long wait_limit;         // iterations of a bounded wait before it gives up
   // block mapping: pattern p owns blocks [pre[p], pre[p+1]); each block covers
   // one orbit and cpb chunks of VEC*blockDim spectator elements
   int64_t pre[9];
@@ -177,6 +196,26 @@ struct KParams {
   int64_t norb[8];              // orbits per pattern
   int64_t ngroup;               // general kernel: total orbit-element groups
   int64_t gpre[9];              // general kernel: group prefix per pattern
+};
+
+// a planned single problem (host side)
+struct Launch {
+  KParams kp;
+  int ar = AR_STRICT;
+  int kernel = 0;  // 0 = K1 (registers), 1 = KG (general strides), 2 = K1T (TMA-staged)
+  int vec = 1;
+  bool empty = false;
+};
+
+// device image of a batch (plan memory, or the library's fixed array): the
+// parameters, K1-block prefix sums and vector widths of its problems, grouped
+// by (d, arithmetic) class; class c uses probs[first_c ..] and the prefix
+// segment starting at prefix[pfirst_c] (n_c + 1 entries)
+template <int NMAX>
+struct BatchImage {
+  KParams probs[NMAX];
+  int64_t prefix[NMAX + 8];
+  int vec[NMAX];
 };
 
 }  // namespace ss

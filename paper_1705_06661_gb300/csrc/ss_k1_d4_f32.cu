@@ -5,8 +5,8 @@ namespace ss {
 
 cudaError_t launch_k1_d4_f32(const KParams& kp, int vec, cudaStream_t st) {
   const dim3 grid((unsigned)kp.pre[npatterns(4)]), block(256);
-  if (vec >= 2) k1_kernel<4, AR_F32, 2, float><<<grid, block, 0, st>>>(kp);
-  else k1_kernel<4, AR_F32, 1, float><<<grid, block, 0, st>>>(kp);
+  (void)vec;
+  k1_kernel<4, AR_F32, 1, float><<<grid, block, 0, st>>>(kp);
   return cudaGetLastError();
 }
 }  // namespace ss

@@ -1,0 +1,15 @@
+// Instantiates part of the spin-summation kernels (see ss_kernels.cuh).
+#include "ss_kernels.cuh"
+
+namespace ss {
+
+cudaError_t launch_kb_d4_exact(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                              cudaStream_t st, const void** fn) {
+  if (fn) {
+    *fn = reinterpret_cast<const void*>(&kb_kernel<4, AR_EXACT, double>);
+    return cudaSuccess;
+  }
+  kb_kernel<4, AR_EXACT, double><<<dim3((unsigned)grid), dim3(256), 0, st>>>(probs, prefix, vecs, n);
+  return cudaGetLastError();
+}
+}  // namespace ss

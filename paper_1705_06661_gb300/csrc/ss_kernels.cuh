@@ -28,19 +28,17 @@
 
 namespace ss {
 
+// pattern tables evaluated once per (D, P); loads from them fold to constants
+// in the unrolled loops
+template <int D, int P>
+__device__ constexpr Pattern<D> kPattern = make_pattern<D>(P);
+
 template <int D, int P>
 struct Pat {
   static constexpr int M = make_pattern<D>(P).m;
   static constexpr int ND = make_pattern<D>(P).nd;
-  // table lookups; called with unrolled (compile-time) indices, so they fold to constants
-  __device__ __forceinline__ static int lab(int u, int k) {
-    constexpr Pattern<D> pt = make_pattern<D>(P);
-    return pt.lab[u][k];
-  }
-  __device__ __forceinline__ static int idx(int u, int s) {
-    constexpr Pattern<D> pt = make_pattern<D>(P);
-    return pt.idx[u][s];
-  }
+  __device__ __forceinline__ static int lab(int u, int k) { return kPattern<D, P>.lab[u][k]; }
+  __device__ __forceinline__ static int idx(int u, int s) { return kPattern<D, P>.idx[u][s]; }
 };
 
 // C(n, k) for k <= 4 with constant divisors (no 64-bit division routine);
@@ -208,13 +206,13 @@ __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>:
     float t[M];
 #pragma unroll
     for (int u = 0; u < M; u++) t[u] = x[u];
-    auto stage = [&](const double* cd) {
+    auto stage = [&](const float* cf) {
       float acc[M];
 #pragma unroll
       for (int u = 0; u < M; u++) acc[u] = 0.f;
 #pragma unroll
       for (int s = 0; s < NS; s++) {
-        const float c = (float)cd[s];
+        const float c = cf[s];
         if (c != 0.f) {
 #pragma unroll
           for (int u = 0; u < M; u++) acc[u] = fmaf(c, t[Pat<D, P>::idx(u, s)], acc[u]);
@@ -225,9 +223,9 @@ __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>:
     };
 #pragma unroll
     for (int st = 0; st < 3; st++)
-      if (st < kp.nstage) stage(kp.cd[st]);
-    for (int st = 3; st < kp.nstage; st++) stage(kp.cd[st]);
-    const float al = (float)kp.alpha;
+      if (st < kp.nstage) stage(kp.cf[st]);
+    for (int st = 3; st < kp.nstage; st++) stage(kp.cf[st]);
+    const float al = kp.alphaf;
 #pragma unroll
     for (int u = 0; u < M; u++) y[u] = al * t[u];
   } else {
@@ -245,6 +243,12 @@ __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>:
       for (int u = 0; u < M; u++) y[u] = __dmul_rn(kp.alpha, x[u]);
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ T beta_of(const KParams& kp) {
+  if constexpr (sizeof(T) == 8) return kp.beta;
+  else return kp.betaf;
 }
 
 // B = alpha S(A) + beta B_old: the beta term, in the reference order for FP64
@@ -291,6 +295,7 @@ template <int D, int P, int AR, int VEC, typename T>
 __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t c0, int64_t c1) {
   constexpr int M = Pat<D, P>::M;
   __shared__ int64_t soff[2][24];
+  __syncthreads();
   if (threadIdx.x < 32) {
     int val[4] = {0, 0, 0, 0};
     unrank<Pat<D, P>::ND>(orb, kp.O, val);
@@ -327,7 +332,7 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
 #pragma unroll
     for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T>(kp, x[e], y[e]);
     const bool beta = kp.flags & KF_BETA;
-    const T bt = (T)kp.beta;
+    const T bt = beta_of<T>(kp);
 #pragma unroll
     for (int u = 0; u < M; u++) {
       T v[VEC];
@@ -354,9 +359,10 @@ __device__ __forceinline__ int find_pattern(const int64_t* pre, int64_t b) {
   return p;
 }
 
+// one K1 block of work: block index b of the problem's grid -> (pattern,
+// orbit, chunk range)
 template <int D, int AR, int VEC, typename T>
-__global__ void __launch_bounds__(256) k1_kernel(const __grid_constant__ KParams kp) {
-  const int64_t b = blockIdx.x;
+__device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   const int p = find_pattern<D>(kp.pre, b);
   const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;  // blocks per orbit
   const int64_t local = b - kp.pre[p];
@@ -378,6 +384,55 @@ __global__ void __launch_bounds__(256) k1_kernel(const __grid_constant__ KParams
           case 7: k1_body<D, 7, AR, VEC, T>(kp, orb, c0, c1); break;
         }
       }
+  }
+}
+
+template <int D, int AR, int VEC, typename T>
+__global__ void __launch_bounds__(256) k1_kernel(const __grid_constant__ KParams kp) {
+  k1_block<D, AR, VEC, T>(kp, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// KB: batched persistent kernel. A fixed grid walks the K1 blocks of n
+// problems with a grid stride; block g belongs to the problem i with
+// prefix[i] <= g < prefix[i + 1] (binary search). A CTA copies a problem's
+// parameters into shared memory when the problem changes, then runs that K1
+// block. One launch covers all problems of one (d, arithmetic) class.
+// ---------------------------------------------------------------------------
+template <int D, int AR, typename T>
+__device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int64_t b) {
+  constexpr int VMAX = sizeof(T) == 8 ? (D == 3 ? 2 : 1) : (D == 3 ? 4 : 1);
+  if constexpr (VMAX >= 4) {
+    if (vec == 4) { k1_block<D, AR, 4, T>(kp, b); return; }
+  }
+  if constexpr (VMAX >= 2) {
+    if (vec == 2) { k1_block<D, AR, 2, T>(kp, b); return; }
+  }
+  k1_block<D, AR, 1, T>(kp, b);
+}
+
+template <int D, int AR, typename T>
+__global__ void __launch_bounds__(256) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
+                                                 const int* __restrict__ vecs, int n) {
+  __shared__ KParams skp;
+  const int64_t total = prefix[n];
+  int cur = -1;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    if (lo != cur) {
+      __syncthreads();
+      const int4* src = reinterpret_cast<const int4*>(probs + lo);
+      int4* dst = reinterpret_cast<int4*>(&skp);
+      for (int i = threadIdx.x; i < (int)(sizeof(KParams) / 16); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      cur = lo;
+    }
+    k1_block_anyvec<D, AR, T>(skp, vecs[lo], g - prefix[lo]);
   }
 }
 
@@ -418,7 +473,7 @@ __device__ __forceinline__ void kg_body(const KParams& kp, int64_t g) {
 #pragma unroll
   for (int u = 0; u < M; u++) x[u] = A[offA[u]];
   apply_group<D, P, AR, T>(kp, x, y);
-  const T bt = (T)kp.beta;
+  const T bt = beta_of<T>(kp);
 #pragma unroll
   for (int u = 0; u < M; u++) B[offB[u]] = (kp.flags & KF_BETA) ? add_beta(y[u], B[offB[u]], bt) : y[u];
 }

@@ -1,5 +1,5 @@
 // Device status word and the dispatch from (d, arithmetic, vector width) to
-// the kernel instantiations of the ss_k*.cu translation units.
+// the kernel instantiations of the ss_k1_*, ss_kg_* and ss_kb_* translation units.
 #include <cuda_runtime.h>
 
 #include "ss_internal.h"
@@ -14,6 +14,15 @@ cudaError_t launch_k1_d4_strict(const KParams& kp, cudaStream_t st);
 cudaError_t launch_k1_d4_f32(const KParams& kp, int vec, cudaStream_t st);
 cudaError_t launch_kg_d3(const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_kg_d4(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k1t_d3(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_kb_d3(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                         cudaStream_t st, const void** fn);
+cudaError_t launch_kb_d4_exact(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                              cudaStream_t st, const void** fn);
+cudaError_t launch_kb_d4_strict(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                              cudaStream_t st, const void** fn);
+cudaError_t launch_kb_d4_f32(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                              cudaStream_t st, const void** fn);
 
 cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st) {
   if (d == 3) return launch_k1_d3(kp, ar, vec, st);
@@ -22,8 +31,42 @@ cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st
   return launch_k1_d4_f32(kp, vec, st);
 }
 
+// TMA-staged orbit stream (3D; exact FP64 or FP32 arithmetic)
+cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st) {
+  if (d != 3) return cudaErrorInvalidValue;
+  return launch_k1t_d3(kp, ar, st);
+}
+
+// elements per member chunk of the K1T instantiations
+int k1t_chunk(int d, int ar) {
+  (void)d;
+  return SS_K1T3_NCW * 32 * (ar == AR_EXACT ? 2 : 4);
+}
+
+// device address of the status word, per device
+int* status_ptr() {
+  static int* ptr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st) {
   return d == 3 ? launch_kg_d3(kp, ar, st) : launch_kg_d4(kp, ar, st);
+}
+
+// batched kernel of class (d, ar); with fn != nullptr only reports the kernel symbol
+cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                      cudaStream_t st, const void** fn) {
+  if (d == 3) return launch_kb_d3(ar, probs, prefix, vecs, n, grid, st, fn);
+  if (ar == AR_EXACT) return launch_kb_d4_exact(probs, prefix, vecs, n, grid, st, fn);
+  if (ar == AR_STRICT) return launch_kb_d4_strict(probs, prefix, vecs, n, grid, st, fn);
+  return launch_kb_d4_f32(probs, prefix, vecs, n, grid, st, fn);
 }
 
 cudaError_t read_and_clear_status(int* out) {

@@ -205,9 +205,20 @@ def test_exact_path_parameters(lib):
 
 
 def test_launch_shape(lib):
+    # aligned dense spectator blocks: the register orbit stream (kernel 0) with 16-byte vectors for 3D
     _, info, _, _ = debug_plan(lib, 3, 16, 48, wl.table2(1))
     assert info["kernel"] == 0 and info["vec"] == 2
     _, info, _, _ = debug_plan(lib, 4, 12, 12, wl.table2(5))
+    assert info["kernel"] == 0 and info["vec"] == 1
+    # SPINSUM_TMA (8) selects the TMA-staged orbit stream (kernel 2) for 3D, not for 4D or strict
+    _, info, _, _ = debug_plan(lib, 3, 16, 48, wl.table2(1), mode=8)
+    assert info["kernel"] == 2
+    _, info, _, _ = debug_plan(lib, 4, 12, 12, wl.table2(5), mode=8)
+    assert info["kernel"] == 0
+    _, info, _, _ = debug_plan(lib, 3, 16, 48, wl.table2(1), mode=8 | 4)
+    assert info["kernel"] == 0
+    # odd spectator block (S = 27 * 27 * 27 is odd): no 16-byte runs, scalar register path
+    _, info, _, _ = debug_plan(lib, 3, 8, 27, wl.table2(1))
     assert info["kernel"] == 0 and info["vec"] == 1
     _, info, _, _ = debug_plan(lib, 3, 16, 3, wl.table2(1))   # 27 spectators: general kernel
     assert info["kernel"] == 1
