@@ -147,6 +147,33 @@ int spinsum_plan_destroy(spinsum_plan* plan);
 /* description of the plan's tuning choice, e.g. "vec=2 block=256 split=1" */
 const char* spinsum_plan_describe(const spinsum_plan* plan);
 
+/*
+ * spinsum_batch_static -- the batched summation without any device allocation.
+ * The paper has no counterpart: this is a deployment feature of the library.
+ *
+ * Some callers cannot call cudaMalloc: codes that reserve nearly all of HBM
+ * for their amplitude tensors up front and hand out memory only from their
+ * own pool, and latency-bound services where a cudaMalloc (and the device
+ * synchronization it can imply) may not happen on the request path. For them
+ * this entry point runs the same batched kernel as a plan, but reads the
+ * per-problem parameters and block prefix sums from one fixed array that the
+ * library keeps in device memory from load until process exit (about 400 KB
+ * on every GPU that loads the library). The caller still owns and passes every
+ * input and output tensor.
+ *
+ * problems, nproblems, dtype: as for spinsum_plan_create; at most
+ *   SPINSUM_STATIC_MAX_PROBLEMS problems, else SPINSUM_ERR_ARG.
+ * The call copies the parameters into the array with cudaMemcpyAsync on
+ * `stream`, then launches there; it calls no allocating routine. The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array and overwrite what they use: calls whose work
+ * can overlap on the GPU (for example on two streams at once) race on it, and
+ * the caller must order them.
+ */
+#define SPINSUM_STATIC_MAX_PROBLEMS 64
+int spinsum_batch_static(const spinsum_problem* problems, int nproblems, int dtype, spinsum_stream_t stream);
+
 /* Synchronizes `stream`, then reads and clears the device status word:
  * SPINSUM_OK, SPINSUM_ERR_TIMEOUT or SPINSUM_ERR_DEVICE. */
 int spinsum_check_status(spinsum_stream_t stream);

@@ -30,6 +30,7 @@ SPINSUM_FACTORIZED = 1
 SPINSUM_ADJOINT = 2
 SPINSUM_STRICT = 4
 SPINSUM_TMA = 8
+SPINSUM_STATIC_MAX_PROBLEMS = 64
 
 _STATUS_NAMES = {
     -1: "SPINSUM_ERR_ARG", -2: "SPINSUM_ERR_ALIAS", -3: "SPINSUM_ERR_UNSUPPORTED", -4: "SPINSUM_ERR_CUDA",
@@ -84,6 +85,8 @@ def _load() -> ctypes.CDLL:
     lib.spinsum_plan_destroy.restype = ctypes.c_int
     lib.spinsum_plan_describe.argtypes = [_VP]
     lib.spinsum_plan_describe.restype = ctypes.c_char_p
+    lib.spinsum_batch_static.argtypes = [ctypes.POINTER(spinsum_problem), ctypes.c_int, ctypes.c_int, _VP]
+    lib.spinsum_batch_static.restype = ctypes.c_int
     lib.spinsum_check_status.argtypes = [_VP]
     lib.spinsum_check_status.restype = ctypes.c_int
     lib.spinsum_last_error.argtypes = []
@@ -155,6 +158,12 @@ def spinsum_plan_create(problems, dtype, allow_tuning_runs, stream):
     _check(lib.spinsum_plan_create(ctypes.byref(h), arr, len(problems), int(dtype), int(allow_tuning_runs),
                                    _VP(stream)))
     return h
+
+
+def spinsum_batch_static(problems, dtype, stream) -> int:
+    """problems: list of spinsum_problem; runs the batch without allocating device memory."""
+    arr = (spinsum_problem * len(problems))(*problems)
+    return _check(lib.spinsum_batch_static(arr, len(problems), int(dtype), _VP(stream)))
 
 
 def spinsum_plan_execute(plan, stream) -> int:

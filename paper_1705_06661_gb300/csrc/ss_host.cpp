@@ -24,6 +24,7 @@ cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st);
 int k1t_chunk(int d, int ar);
 
 int* status_ptr();
+cudaError_t static_scratch_ptr(void** out);
 cudaError_t read_and_clear_status(int* out);
 }  // namespace ss
 
@@ -790,6 +791,79 @@ int spinsum_plan_destroy(spinsum_plan* plan) {
 const char* spinsum_plan_describe(const spinsum_plan* plan) { return plan ? plan->desc.c_str() : ""; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// spinsum_batch_static: the batched kernel with its image in the library's
+// fixed device array (ss_static.cu) instead of plan memory. Nothing is
+// allocated: the image is built on the host, copied into the array with
+// cudaMemcpyAsync on the caller's stream, and the kernels read it there.
+// ---------------------------------------------------------------------------
+extern "C" int spinsum_batch_static(const spinsum_problem* problems, int nproblems, int dtype,
+                                    spinsum_stream_t stream) {
+  t_err.clear();
+  if (nproblems < 0 || (nproblems > 0 && !problems)) return fail(SPINSUM_ERR_ARG, "bad problem list");
+  if (nproblems > SPINSUM_STATIC_MAX_PROBLEMS)
+    return fail(SPINSUM_ERR_ARG, "spinsum_batch_static takes at most %d problems (got %d)",
+                SPINSUM_STATIC_MAX_PROBLEMS, nproblems);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<Launch> launches;
+  for (int i = 0; i < nproblems; i++) {
+    const spinsum_problem& q = problems[i];
+    Request r{q.d, dtype, q.ext, q.A, q.lda, q.B, q.ldb, q.coef, q.nfactors, q.mode & ~SPINSUM_TMA, q.alpha,
+              q.beta, q.inplace};
+    Launch L;
+    int rc = plan_one(r, &L);
+    if (rc != SPINSUM_OK) {
+      std::string m = "problem " + std::to_string(i) + ": " + t_err;
+      return fail(rc, "%s", m.c_str());
+    }
+    if (!L.empty) launches.push_back(L);
+  }
+  if (launches.empty()) return SPINSUM_OK;
+  void* dimg = nullptr;
+  cudaError_t e = static_scratch_ptr(&dimg);
+  if (e != cudaSuccess) return cuda_fail(e, "looking up the static scratch array");
+  const int nmax = SPINSUM_STATIC_MAX_PROBLEMS;
+  std::vector<unsigned char> img(batch_image_bytes(nmax), 0);
+  BatchLayout lay{reinterpret_cast<KParams*>(img.data() + batch_offset_probs(nmax)),
+                  reinterpret_cast<int64_t*>(img.data() + batch_offset_prefix(nmax)),
+                  reinterpret_cast<int*>(img.data() + batch_offset_vec(nmax))};
+  std::vector<int> order(launches.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+  const std::vector<ClassRange> cls = fill_batch(launches, order, 0, lay, status_ptr());
+  if (!cls.empty()) {
+    // every field a kernel reads is rewritten here; unused entries stay zero
+    e = cudaMemcpyAsync(dimg, img.data(), img.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the batch parameters");
+  }
+  const unsigned char* base = static_cast<const unsigned char*>(dimg);
+  const KParams* probs = reinterpret_cast<const KParams*>(base + batch_offset_probs(nmax));
+  const int64_t* prefix = reinterpret_cast<const int64_t*>(base + batch_offset_prefix(nmax));
+  const int* vec = reinterpret_cast<const int*>(base + batch_offset_vec(nmax));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (const ClassRange& c : cls) {
+    const void* fn = nullptr;
+    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, 0, st, &fn);
+    int nb = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.blocks, (int64_t)sms * std::max(1, nb)));
+    e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, grid, st, nullptr);
+    t_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "static batched kernel launch");
+  }
+  for (const Launch& L : launches) {
+    if (L.kernel != 1) continue;
+    KParams kp = L.kp;
+    kp.status = status_ptr();
+    e = launch_kg(kp.nspec, kp, L.ar, st);
+    t_launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "general kernel launch");
+  }
+  return SPINSUM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Planner introspection for host-side tests (not part of the public ABI):

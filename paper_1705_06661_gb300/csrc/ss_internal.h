@@ -207,6 +207,13 @@ struct Launch {
   bool empty = false;
 };
 
+// byte layout of a batch image for at most n problems: KParams[n], then the
+// prefix segments (n + 8 int64), then the vector widths (n int)
+constexpr size_t batch_offset_probs(int n) { return (void)n, 0; }
+constexpr size_t batch_offset_prefix(int n) { return sizeof(KParams) * (size_t)n; }
+constexpr size_t batch_offset_vec(int n) { return batch_offset_prefix(n) + sizeof(int64_t) * (size_t)(n + 8); }
+constexpr size_t batch_image_bytes(int n) { return batch_offset_vec(n) + sizeof(int) * (size_t)n; }
+
 // device image of a batch (plan memory, or the library's fixed array): the
 // parameters, K1-block prefix sums and vector widths of its problems, grouped
 // by (d, arithmetic) class; class c uses probs[first_c ..] and the prefix
