@@ -318,8 +318,17 @@ int plan_one(const Request& r, Launch* L) {
     int a = 0;
     const bool apow2 = pow2(r.alpha, &a);
     if (ok && Lnorm >= 1.0 && Lnorm <= 127.0) {
-      int W = 26;
-      while (W > 0 && Lnorm * std::ldexp(1.0, W) > 2147483647.0) W--;
+      // limb width W: every limb sum, plus the rounding increment of the low
+      // limb, stays below 2^31; kdrop rounds the joined sum to below 2^50
+      int W = 26, kdrop = 0;
+      for (;;) {
+        kdrop = 0;
+        const double ymax = Lnorm * (std::ldexp(1.0, 2 * W) + std::ldexp(1.0, W));
+        while (ymax / std::ldexp(1.0, kdrop) + 1.0 >= std::ldexp(1.0, 50)) kdrop++;
+        const double rnd = kdrop ? std::ldexp(1.0, kdrop - 1) : 0.0;
+        if (W == 0 || Lnorm * std::ldexp(1.0, W) + rnd <= 2147483647.0) break;
+        W--;
+      }
       if (2 * W >= 48) {
         // expanded integer coefficients for the orbit matrices: product of the scaled stages
         std::vector<long long> ex(g.n, 0);
@@ -336,9 +345,6 @@ int plan_one(const Request& r, Launch* L) {
         }
         const bool neg = apow2 && r.alpha < 0;
         int aexp = -escale + (apow2 ? a : 0);
-        int kdrop = 0;
-        const double ymax = Lnorm * (std::ldexp(1.0, 2 * W) + std::ldexp(1.0, W));
-        while (ymax / std::ldexp(1.0, kdrop) + 1.0 >= std::ldexp(1.0, 50)) kdrop++;
         const int cshift = 53 - 2 * W + kdrop + aexp;
         const int emin = std::max(64, 1 - cshift), emax = std::min(2046, 2046 - cshift);
         if (emin <= emax) {
@@ -347,6 +353,7 @@ int plan_one(const Request& r, Launch* L) {
           kp.W = W;
           kp.s0 = 53 - 2 * W;
           kp.kdrop = kdrop;
+          kp.wk = W - kdrop;
           kp.rnd = kdrop ? (1LL << (kdrop - 1)) : 0;
           if (kdrop) kp.flags |= KF_KDROP;
           if (!apow2) kp.flags |= KF_ALPHA_MUL;
@@ -359,6 +366,13 @@ int plan_one(const Request& r, Launch* L) {
               kp.ci[st][s] = (int)((neg && st + 1 == ist.size()) ? -ist[st][s] : ist[st][s]);
           if (neg)
             for (auto& v : ex) v = -v;
+          if (d == 4) {
+            // d = 4: the generic orbit always applies the expanded operator (identical
+            // results in exact arithmetic), which lets the kernel keep one group of
+            // outputs live at a time
+            kp.nci = 1;
+            for (int s = 0; s < g.n; s++) kp.ci[0][s] = (int)ex[s];
+          }
           if (d == 3) fill_mp<3>(ex, kp.mp);
           else fill_mp<4>(ex, kp.mp);
         }

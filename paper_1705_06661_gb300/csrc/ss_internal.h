@@ -178,6 +178,7 @@ struct alignas(16) KParams {
   int W;                        // limb width; grid = 2^(E+1-2W) of the orbit element's max
   int s0;                       // 53 - 2W
   int kdrop;                    // low bits rounded off the sum before conversion
+  int wk;                       // W - kdrop
   long long rnd;                // 2^(kdrop-1) or 0
   int cexp;                     // added to the max exponent field to build the conversion constant
   unsigned emin, emax;          // fast path when the max exponent field lies in [emin, emax]

@@ -118,23 +118,31 @@ __device__ __forceinline__ void strict_core(const KParams& kp, double (&t)[Pat<D
 // Returns false (and leaves y untouched) when E is outside [emin, emax]:
 // zero or tiny groups, huge values, infinities and NaNs take the strict core.
 // ---------------------------------------------------------------------------
-template <int D, int P>
-__device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[Pat<D, P>::M],
-                                           double (&y)[Pat<D, P>::M]) {
-  constexpr int M = Pat<D, P>::M;
-  constexpr int NS = fact(D);
+// shared prologue: largest exponent field E of the group and the signed limbs
+template <int M>
+__device__ __forceinline__ bool exact_limbs(const KParams& kp, const double (&x)[M], int (&l0)[M], int (&l1)[M],
+                                            unsigned& E) {
   unsigned hi[M], lo[M];
-  unsigned E = 0;
+  E = 0;
 #pragma unroll
   for (int v = 0; v < M; v++) {
     hi[v] = (unsigned)__double2hiint(x[v]);
     lo[v] = (unsigned)__double2loint(x[v]);
     E = max(E, hi[v] & 0x7FF00000u);
   }
-  if (E < kp.emin || E > kp.emax) return false;
+  if (E < kp.emin || E > kp.emax) {
+    // a group of exact zeros (signed or not) is exact on any grid: give it the
+    // smallest valid exponent and let the fixed-point path produce +0
+    unsigned any = 0;
+    if (E == 0) {
+#pragma unroll
+      for (int v = 0; v < M; v++) any |= (hi[v] & 0x7FFFFFFFu) | lo[v];
+    }
+    if (E != 0 || any != 0) return false;
+    E = kp.emin;
+  }
   const int W = kp.W;
   const unsigned mask = (1u << W) - 1u;
-  int l0[M], l1[M];
 #pragma unroll
   for (int v = 0; v < M; v++) {
     unsigned k = ((E - (hi[v] & 0x7FF00000u)) >> 20) + (unsigned)kp.s0;
@@ -146,11 +154,33 @@ __device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[
     l0[v] = (a ^ sg) - sg;
     l1[v] = (b ^ sg) - sg;
   }
+  return true;
+}
+
+// limbs (y1 * 2^W + y0) -> FP64: round off kdrop bits on the low limb
+// ((y1 2^W + y0 + r) >> k = y1 2^(W-k) + ((y0 + r) >> k) for k <= W), then one
+// subtraction of the magic constant C = chi:0
+__device__ __forceinline__ double exact_out(const KParams& kp, unsigned chi, double C, int y0, int y1) {
+  const long long Y = ((long long)y1 << kp.wk) + (long long)((y0 + (int)kp.rnd) >> kp.kdrop);
+  const double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
+  return __dsub_rn(Dv, C);
+}
+
+template <int D, int P, int NST = 0>
+__device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[Pat<D, P>::M],
+                                           double (&y)[Pat<D, P>::M]) {
+  constexpr int M = Pat<D, P>::M;
+  constexpr int NS = fact(D);
+  int l0[M], l1[M];
+  unsigned E;
+  if (!exact_limbs<M>(kp, x, l0, l1, E)) return false;
   int y0[M], y1[M];
   if constexpr (P == 0) {
+    // NST > 0: the stage count is a compile-time constant (only those stages are
+    // compiled); NST == 0: up to MAXSTAGE_EXACT stages, count read at run time
 #pragma unroll
-    for (int st = 0; st < MAXSTAGE_EXACT; st++) {
-      if (st >= kp.nci) break;
+    for (int st = 0; st < (NST > 0 ? NST : MAXSTAGE_EXACT); st++) {
+      if (NST == 0 && st >= kp.nci) break;
 #pragma unroll
       for (int u = 0; u < M; u++) { y0[u] = 0; y1[u] = 0; }
 #pragma unroll
@@ -186,11 +216,40 @@ __device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[
   const unsigned chi = E + (unsigned)kp.cexp;
   const double C = __hiloint2double((int)chi, 0);
 #pragma unroll
-  for (int u = 0; u < M; u++) {
-    long long Y = ((long long)l1[u] << W) + (long long)l0[u];
-    if (kp.flags & KF_KDROP) Y = (Y + kp.rnd) >> kp.kdrop;
-    double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
-    y[u] = __dsub_rn(Dv, C);
+  for (int u = 0; u < M; u++) y[u] = exact_out(kp, chi, C, l0[u], l1[u]);
+  return true;
+}
+
+// The generic 24-member orbit of d = 4 with the expanded operator (ci[0]),
+// computed in G groups of 24 / G outputs: only the 48 input limbs and one
+// group's accumulators are live, and each group's outputs go to `sink(u, y)`
+// as soon as they are converted (register pressure, hence occupancy).
+template <int G, class Sink>
+__device__ __forceinline__ bool exact_core_grouped4(const KParams& kp, const double (&x)[24], Sink&& sink) {
+  constexpr int M = 24, NU = M / G;
+  int l0[M], l1[M];
+  unsigned E;
+  if (!exact_limbs<M>(kp, x, l0, l1, E)) return false;
+  const unsigned chi = E + (unsigned)kp.cexp;
+  const double C = __hiloint2double((int)chi, 0);
+#pragma unroll
+  for (int g = 0; g < G; g++) {
+    int y0[NU], y1[NU];
+#pragma unroll
+    for (int j = 0; j < NU; j++) { y0[j] = 0; y1[j] = 0; }
+#pragma unroll
+    for (int s = 0; s < 24; s++) {
+      const int c = kp.ci[0][s];
+      if (c != 0) {
+#pragma unroll
+        for (int j = 0; j < NU; j++) {
+          y0[j] += c * l0[Pat<4, 0>::idx(g * NU + j, s)];
+          y1[j] += c * l1[Pat<4, 0>::idx(g * NU + j, s)];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NU; j++) sink(g * NU + j, exact_out(kp, chi, C, y0[j], y1[j]));
   }
   return true;
 }
@@ -198,7 +257,7 @@ __device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[
 // ---------------------------------------------------------------------------
 // one orbit element group: x (inputs, m members) -> y (outputs), incl. alpha/beta
 // ---------------------------------------------------------------------------
-template <int D, int P, int AR, typename T>
+template <int D, int P, int AR, typename T, int NST = 0>
 __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>::M], T (&y)[Pat<D, P>::M]) {
   constexpr int M = Pat<D, P>::M;
   constexpr int NS = fact(D);
@@ -231,7 +290,7 @@ __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>:
   } else {
     bool done = false;
     if constexpr (AR == AR_EXACT) {
-      done = exact_core<D, P>(kp, x, y);
+      done = exact_core<D, P, NST>(kp, x, y);
       if (done && (kp.flags & KF_ALPHA_MUL)) {
 #pragma unroll
         for (int u = 0; u < M; u++) y[u] = __dmul_rn(kp.alpha, y[u]);
@@ -286,12 +345,33 @@ __device__ __forceinline__ void vstore(T* p, const T (&v)[VEC]) {
   *reinterpret_cast<V*>(p) = w;
 }
 
+// The strict core for one generic d = 4 group whose exponents leave the
+// fixed-point range (zeros, tiny or huge values, Inf, NaN): reloads its 24
+// inputs (nothing of the group has been stored yet, so this is safe in place)
+// and stores alpha S(x) + beta B. Kept out of line: it is rare, and inlining
+// it would hold registers in the hot path.
+static __device__ __noinline__ void strict_fallback_generic4(const KParams& kp, const int64_t* offA, const int64_t* offB,
+                                                      int64_t s) {
+  const double* A = static_cast<const double*>(kp.A);
+  double* B = static_cast<double*>(kp.B);
+  double x[24];
+  for (int u = 0; u < 24; u++) x[u] = A[offA[u] + s];
+  strict_core<4, 0>(kp, x);
+  const bool beta = kp.flags & KF_BETA;
+  for (int u = 0; u < 24; u++) {
+    double* dst = B + offB[u] + s;
+    double v = __dmul_rn(kp.alpha, x[u]);
+    if (beta) v = add_beta(v, *dst, kp.beta);
+    *dst = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K1 body for pattern P. Warp 0 unranks the orbit and writes the m member
 // offsets of A and B to shared memory; the CTA then streams cpb chunks of
 // VEC * blockDim spectator positions through registers.
 // ---------------------------------------------------------------------------
-template <int D, int P, int AR, int VEC, typename T>
+template <int D, int P, int AR, int VEC, typename T, int NST = 0>
 __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t c0, int64_t c1) {
   constexpr int M = Pat<D, P>::M;
   __shared__ int64_t soff[2][24];
@@ -329,8 +409,19 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
 #pragma unroll
       for (int e = 0; e < VEC; e++) x[e][u] = v[e];
     }
+    if constexpr (D == 4 && P == 0 && AR == AR_EXACT && VEC == 1) {
+      const bool beta = kp.flags & KF_BETA, amul = kp.flags & KF_ALPHA_MUL;
+      auto sink = [&](int u, double v) {
+        T* dst = B + soff[1][u] + s;
+        if (amul) v = __dmul_rn(kp.alpha, v);
+        if (beta) v = add_beta(v, *dst, kp.beta);
+        *dst = v;
+      };
+      if (!exact_core_grouped4<4>(kp, x[0], sink)) strict_fallback_generic4(kp, soff[0], soff[1], s);
+      continue;
+    }
 #pragma unroll
-    for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T>(kp, x[e], y[e]);
+    for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T, NST>(kp, x[e], y[e]);
     const bool beta = kp.flags & KF_BETA;
     const T bt = beta_of<T>(kp);
 #pragma unroll
@@ -388,7 +479,7 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
 }
 
 template <int D, int AR, int VEC, typename T>
-__global__ void __launch_bounds__(256) k1_kernel(const __grid_constant__ KParams kp) {
+__global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? 3 : 1) k1_kernel(const __grid_constant__ KParams kp) {
   k1_block<D, AR, VEC, T>(kp, blockIdx.x);
 }
 
