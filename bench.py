@@ -38,15 +38,26 @@ WORKLOAD = "3d-spinsum fp64 A[48,48,48,16,16,16] Table-II-row-1 factorized out-o
 SHAPE = (48, 48, 48, 16, 16, 16)
 D = 3
 
+# smaller workloads of the same kernels for profiler captures (--case); the
+# default case is the benchmark workload above
+CASES = {
+    "3d": (3, (48, 48, 48, 16, 16, 16), 1),
+    "3d-small": (3, (24, 24, 24, 16, 16, 16), 1),     # 453 MB per tensor: above L2, one ncu capture
+    "4d": (4, (12,) * 8, 5),
+    "4d-small": (4, (8, 8, 8, 8, 12, 12, 12, 12), 5),
+}
+
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extra", action="store_true", help="skip the extra per-case lines")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    p.add_argument("--case", default="3d", choices=sorted(CASES),
+                   help="workload: the benchmark (3d) or a smaller one for profiler captures")
     return p.parse_args()
 
 
@@ -78,6 +89,14 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.samples.append((time.time(), line.strip()))
+
+    def wait_first_sample(self, timeout: float = 10.0):
+        """nvidia-smi's start-up can hold the driver for a while; time nothing
+        before its first sample has arrived."""
+        t0 = time.time()
+        while self.proc and not self.samples and time.time() - t0 < timeout:
+            time.sleep(0.05)
+        time.sleep(0.2)
 
     def mark(self, which):
         setattr(self, which, time.time())
@@ -254,17 +273,74 @@ def time_steps(fn, steps, stream, world):
 
 
 def best_of(fn, reps, stream):
+    """(per-launch time of `reps` back-to-back launches, best single launch)"""
     import torch
-    ts = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
     for _ in range(reps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    loop = e0.elapsed_time(e1) / 1e3 / reps
+    ts = []
+    for _ in range(3):
         e0.record(stream)
         fn()
         e1.record(stream)
         e1.synchronize()
         ts.append(e0.elapsed_time(e1) / 1e3)
-    return min(ts), float(np.median(ts))
+    return loop, min(ts)
+
+
+def extra_cases_batched_and_autograd(ss, wl, dev, stream, hbm_peak):
+    """The batched workload (64 uneven 3D blocks, one persistent launch per
+    class, replayed from a CUDA graph; FP64 and FP32 storage) and the
+    differentiable 4D workload (10^8, forward + backward)."""
+    import torch
+    out = []
+    blocks = wl.config4_blocks()
+    for tdt, name in ((torch.float64, "fp64"), (torch.float32, "fp32-storage")):
+        specs, nel = [], 0
+        for pr in blocks:
+            a = ss.colmajor_empty(pr.shape, dtype=tdt, device=dev)
+            a.copy_(torch.from_numpy(wl.uniform(pr.seed, pr.shape)).to(dev))
+            specs.append({"A": a, "B": ss.colmajor_like(a), "coef": pr.coef, "d": 3, "factorized": True})
+            nel += a.numel()
+        plan = ss.Plan(specs, tune=True)
+        g = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream(dev)
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            with torch.cuda.graph(g, stream=s2):
+                plan.execute()
+        stream.wait_stream(s2)
+        mn, one = best_of(g.replay, 10, stream)
+        es = 8 if tdt == torch.float64 else 4
+        out.append({"case": f"batched 64 uneven 3D blocks {name} (graph replay)", "elements": nel,
+                    "GB/s": round(2 * nel * es / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                    "frac": round(2 * nel * es / mn / 1e9 / hbm_peak, 4), "plan": plan.describe()})
+        plan.close()
+        del specs, g
+        torch.cuda.empty_cache()
+    shape = (10,) * 8
+    A = ss.colmajor_empty(shape, device=dev)
+    A.copy_(torch.from_numpy(wl.uniform(4, shape)).to(dev))
+    A.requires_grad_(True)
+    G = ss.colmajor_empty(shape, device=dev)
+    G.copy_(torch.from_numpy(wl.uniform(5, shape)).to(dev))
+    coef = wl.random_coef(4, 105)
+
+    def fwd_bwd():
+        A.grad = None
+        ss.spinsum_autograd(A, coef, d=4).backward(G)
+
+    mn, one = best_of(fwd_bwd, 10, stream)
+    n = A.numel()
+    out.append({"case": "4d 10^8 random set forward+backward (autograd)", "GB/s": round(4 * n * 8 / mn / 1e9, 1),
+                "ms": round(mn * 1e3, 4), "frac": round(4 * n * 8 / mn / 1e9 / hbm_peak, 4)})
+    return out
 
 
 def run_ours(args):
@@ -288,7 +364,7 @@ def run_ours(args):
     A = ss.colmajor_empty(SHAPE, device=dev)
     A.copy_(torch.from_numpy(A_host).to(dev))
     B = ss.colmajor_like(A)
-    coef = wl.table2(1)
+    coef = wl.table2(CASES[args.case][2])
     step = lambda: ss.spinsum(A, coef, d=D, out=B, factorized=True)  # noqa: E731
 
     for _ in range(max(args.warmup, 3)):
@@ -298,7 +374,10 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
+    clocks.wait_first_sample()
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
     ss.spinsum_launch_count(reset=True)
     clocks.mark("t0")
     dt = time_steps(step, args.steps, stream, world)
@@ -315,8 +394,9 @@ def run_ours(args):
 
     # ---- end to end through the public API with pinned host buffers ----
     A_pin = torch.from_numpy(A_host).pin_memory() if True else None
-    B_pin = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(6)))
-    A_pin_cm = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(6)))
+    nd = len(SHAPE)
+    B_pin = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(nd)))
+    A_pin_cm = torch.empty(SHAPE[::-1], dtype=torch.float64).pin_memory().permute(*reversed(range(nd)))
     A_pin_cm.copy_(A_pin)
     del A_pin
 
@@ -332,7 +412,7 @@ def run_ours(args):
     dt_e2e = allmax(world, time_steps(e2e_step, e2e_steps, stream, world))
     e2e_val = world * bytes_step * e2e_steps / dt_e2e / 1e9
     # the result that came back is the result computed on the device
-    assert torch.equal(B_pin[:2, :2, :2, :3, :3, :3], B[:2, :2, :2, :3, :3, :3].cpu())
+    assert torch.equal(B_pin[(slice(0, 2),) * nd], B[(slice(0, 2),) * nd].cpu())
 
     # ---- extra cases: other modes and the 4D workload (not the headline) ----
     extra = []
@@ -351,18 +431,18 @@ def run_ours(args):
         for name, fn in cases:
             for _ in range(2):
                 fn()
-            mn, md = best_of(fn, reps, stream)
-            extra.append({"case": name, "GB/s": round(bytes_step / mn / 1e9, 1), "ms_min": round(mn * 1e3, 4),
-                          "ms_median": round(md * 1e3, 4), "frac": round(bytes_step / mn / 1e9 / hbm_peak, 4)})
+            mn, one = best_of(fn, reps, stream)
+            extra.append({"case": name, "GB/s": round(bytes_step / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                          "ms_single_launch": round(one * 1e3, 4), "frac": round(bytes_step / mn / 1e9 / hbm_peak, 4)})
         del A_pin_cm, B_pin
         A32 = ss.colmajor_empty(SHAPE, dtype=torch.float32, device=dev)
         A32.copy_(A)
         B32 = ss.colmajor_like(A32)
         fn = lambda: ss.spinsum(A32, coef, d=D, out=B32, factorized=True)  # noqa: E731
         fn()
-        mn, md = best_of(fn, reps, stream)
+        mn, one = best_of(fn, reps, stream)
         extra.append({"case": "3d row1 factorized fp32-storage", "GB/s": round(2 * N * 4 / mn / 1e9, 1),
-                      "ms_min": round(mn * 1e3, 4), "frac": round(2 * N * 4 / mn / 1e9 / hbm_peak, 4)})
+                      "ms": round(mn * 1e3, 4), "frac": round(2 * N * 4 / mn / 1e9 / hbm_peak, 4)})
         del A32, B32, A, B
         torch.cuda.empty_cache()
         shape4 = (12,) * 8
@@ -382,9 +462,12 @@ def run_ours(args):
                 fn = lambda c4=c4, kw=kw: ss.spinsum(A4, c4, d=4, out=B4, **kw)  # noqa: E731
             for _ in range(2):
                 fn()
-            mn, md = best_of(fn, reps, stream)
-            extra.append({"case": name, "GB/s": round(2 * n4 * 8 / mn / 1e9, 1), "ms_min": round(mn * 1e3, 4),
-                          "ms_median": round(md * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
+            mn, one = best_of(fn, reps, stream)
+            extra.append({"case": name, "GB/s": round(2 * n4 * 8 / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                          "ms_single_launch": round(one * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
+        del A4, B4
+        torch.cuda.empty_cache()
+        extra += extra_cases_batched_and_autograd(ss, wl, dev, stream, hbm_peak)
         ss.spinsum_check_status(stream.cuda_stream)
 
     cpu = None
@@ -406,7 +489,7 @@ def run_ours(args):
             "frac_of_8TBps": round(value / 8000.0, 4),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4), "peak_source": peak_src,
-                         "traffic": ncu_traffic("3d-row1-factorized-oop"),
+                         "traffic": ncu_traffic(args.case),
                          "algorithmic_bytes_per_launch": bytes_step},
             "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": N * 8,
                     "d2h_bytes_per_step": N * 8, "steps": e2e_steps},
@@ -423,7 +506,14 @@ def run_ours(args):
 
 
 def main():
+    global D, SHAPE, WORKLOAD
     args = parse()
+    if args.case != "3d":
+        d, shape, row = CASES[args.case]
+        D, SHAPE = d, shape
+        WORKLOAD = f"{d}d-spinsum fp64 A{list(shape)} Table-II-row-{row} factorized out-of-place (profiling case)"
+        args.no_extra = True
+        args.no_cpu = True
     if args.impl == "reference":
         run_reference(args)
     else:
