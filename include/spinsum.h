@@ -40,6 +40,7 @@
 #ifndef SPINSUM_H
 #define SPINSUM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -107,6 +108,34 @@ int spinsum_3d(int dtype, const int64_t ext[6], const void* A, const int64_t lda
 int spinsum_4d(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
                const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
                int inplace, spinsum_stream_t stream);
+
+/*
+ * spinsum_3d_host / spinsum_4d_host -- the same summation on tensors in host
+ * memory (pinned memory lets the copies run asynchronously and overlap).
+ *
+ * A and B are host pointers to dense column-major tensors (strides must be
+ * the dense ones; SPINSUM_ERR_UNSUPPORTED otherwise).
+ * Page-locked memory (cudaHostAlloc / cudaHostRegister, mapped): the orbit
+ * kernel reads A and writes B directly over the host link, in one launch that
+ * uses both directions of the link at once; `workspace` is not used and may
+ * be NULL.
+ * Pageable memory: the work is split along the slowest spectator index into
+ * chunks; each chunk is copied to the device (one 2D copy with a row per
+ * permuted tuple), summed there, and copied back, with copy-in, compute and
+ * copy-out of successive chunks overlapped on three internal streams (created
+ * on the first call on each device and kept). The device memory is the
+ * caller's `workspace` of `workspace_bytes` (three chunk slots;
+ * SPINSUM_ERR_ARG with the minimum size if it cannot hold one slice).
+ * The call is asynchronous: `stream` is ordered before and after the whole
+ * pipeline, so a synchronize on `stream` waits for B. Other arguments as for
+ * spinsum_3d / spinsum_4d.
+ */
+int spinsum_3d_host(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
+                    const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
+int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
+                    const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
 
 /*
  * Batched plans: many independent spin summations (uneven extents, mixed d,

@@ -76,6 +76,11 @@ def _load() -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = sig
         f.restype = ctypes.c_int
+    hsig = sig[:-1] + [_VP, ctypes.c_size_t, _VP]
+    for name in ("spinsum_3d_host", "spinsum_4d_host"):
+        f = getattr(lib, name)
+        f.argtypes = hsig
+        f.restype = ctypes.c_int
     lib.spinsum_plan_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(spinsum_problem), ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, _VP]
     lib.spinsum_plan_create.restype = ctypes.c_int
@@ -137,6 +142,30 @@ def spinsum_3d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, in
 def spinsum_4d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream) -> int:
     """spinsum_4d of the C-ABI; A, B and stream are integer addresses."""
     return _call(lib.spinsum_4d, 8, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream)
+
+
+def _call_host(fn, n, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, ws, ws_bytes,
+               stream):
+    if len(ext) != n or len(lda) != n or len(ldb) != n:
+        raise ValueError(f"expected {n} extents and strides")
+    c = _coef(coef)
+    return _check(fn(int(dtype), _i64(ext), _VP(A), _i64(lda), _VP(B), _i64(ldb), _VP(c.ctypes.data),
+                     int(nfactors), int(mode), float(alpha), float(beta), int(inplace), _VP(ws),
+                     ctypes.c_size_t(int(ws_bytes)), _VP(stream)))
+
+
+def spinsum_3d_host(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, workspace,
+                    workspace_bytes, stream) -> int:
+    """spinsum_3d_host of the C-ABI; A and B are host addresses, workspace a device address."""
+    return _call_host(lib.spinsum_3d_host, 6, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta,
+                      inplace, workspace, workspace_bytes, stream)
+
+
+def spinsum_4d_host(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, workspace,
+                    workspace_bytes, stream) -> int:
+    """spinsum_4d_host of the C-ABI; A and B are host addresses, workspace a device address."""
+    return _call_host(lib.spinsum_4d_host, 8, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta,
+                      inplace, workspace, workspace_bytes, stream)
 
 
 def spinsum_check_status(stream) -> int:

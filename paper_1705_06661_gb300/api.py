@@ -90,6 +90,45 @@ def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | 
     return out
 
 
+def spinsum_host(A: torch.Tensor, coef, *, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                 d: int | None = None, factorized: bool = False, adjoint: bool = False, strict: bool = False,
+                 alpha: float = 1.0, beta: float = 0.0, inplace: bool = False,
+                 stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """The summation of a dense column-major CPU tensor (spinsum_3d_host /
+    spinsum_4d_host). Pinned tensors are read and written by the kernel in
+    place over the host link; pageable ones go through a three-stream
+    copy-in / sum / copy-out pipeline in `workspace` (a CUDA byte tensor;
+    default 3/8 of A's bytes, at least three slices). Asynchronous on `stream`:
+    synchronize before reading `out`."""
+    if d is None:
+        d = A.dim() // 2
+    if A.is_cuda:
+        raise ValueError("A must be a CPU tensor")
+    dtype = _b.SPINSUM_F64 if A.dtype == torch.float64 else _b.SPINSUM_F32
+    c = _coef_chain(coef, d)
+    if inplace:
+        out = A
+    elif out is None:
+        out = colmajor_empty(A.shape, dtype=A.dtype, device="cpu")
+    ext, lda = _dims(A, d)
+    _, ldb = _dims(out, d)
+    if workspace is None and A.is_pinned() and out.is_pinned():
+        workspace = torch.empty(0, dtype=torch.uint8, device="cuda")   # zero-copy: no staging memory
+    if workspace is None:
+        slow = max(int(A.shape[d - 1]), 1)
+        per = (A.numel() // slow) * A.element_size() * (2 if (beta != 0.0 and not inplace) else 1)
+        nbytes = 3 * per * max(1, (slow + 7) // 8)
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
+        | (_b.SPINSUM_STRICT if strict else 0)
+    st = (stream or torch.cuda.current_stream(workspace.device)).cuda_stream
+    fn = _b.spinsum_3d_host if d == 3 else _b.spinsum_4d_host
+    with torch.cuda.device(workspace.device):
+        fn(dtype, ext, A.data_ptr(), lda, out.data_ptr(), ldb, c, c.shape[0], mode, alpha, beta, int(inplace),
+           workspace.data_ptr(), workspace.numel(), st)
+    return out
+
+
 class SpinSumFunction(torch.autograd.Function):
     """Differentiable spin summation. The operator is linear, so the gradient
     of B = alpha S(A) is alpha S^T(gB), S^T = sum a_sigma pi_{sigma^-1} for one

@@ -495,6 +495,175 @@ const char* spinsum_version(void) { return "spinsum-gb300 0.1 (sm_103a)"; }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// host-resident tensors: the summation of a column-major host tensor, in
+// chunks along the slowest spectator index; each chunk is copied in (one 2D
+// copy: a row per permuted tuple), summed on the device and copied out, on
+// three internal streams so that copy-in, compute and copy-out of successive
+// chunks overlap. The device memory is the caller's workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HostPipe {
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};   // copy-in, compute, copy-out
+  std::vector<cudaEvent_t> ev;                       // per slot: in, done, free
+  cudaEvent_t start = nullptr, end = nullptr;
+};
+
+int host_pipe(HostPipe** out) {
+  static HostPipe pipes[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(SPINSUM_ERR_UNSUPPORTED, "device index above 63");
+  HostPipe& P = pipes[dev];
+  if (!P.s[0]) {
+    for (auto& st : P.s)
+      if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "creating the pipeline streams");
+    if ((e = cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&P.end, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "creating the pipeline events");
+  }
+  *out = &P;
+  return SPINSUM_OK;
+}
+
+int run_host(const Request& r, void* ws, size_t ws_bytes, cudaStream_t user) {
+  t_err.clear();
+  const int d = r.d;
+  if (d != 3 && d != 4) return fail(SPINSUM_ERR_ARG, "d must be 3 or 4");
+  if (!r.ext || !r.lda || !r.ldb) return fail(SPINSUM_ERR_ARG, "null extent or stride array");
+  if (r.dtype != SPINSUM_F64 && r.dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", r.dtype);
+  const size_t es = r.dtype == SPINSUM_F64 ? 8 : 4;
+  const int nidx = 2 * d;
+  int64_t total = 1, dense[8];
+  for (int k = 0; k < nidx; k++) {
+    if (r.ext[k] < 0) return fail(SPINSUM_ERR_ARG, "negative extent at index %d", k);
+    dense[k] = total;
+    total *= r.ext[k];
+  }
+  if (total == 0) return SPINSUM_OK;
+  for (int k = 0; k < nidx; k++)
+    if ((r.ext[k] > 1 && r.lda[k] != dense[k]) || (r.ext[k] > 1 && r.ldb[k] != dense[k]))
+      return fail(SPINSUM_ERR_UNSUPPORTED, "host tensors must be dense column-major");
+  if (!r.A || !r.B) return fail(SPINSUM_ERR_ARG, "null tensor pointer");
+  if (r.inplace && r.A != r.B) return fail(SPINSUM_ERR_ALIAS, "inplace requires A == B");
+  if (!r.inplace) {
+    const uintptr_t a0 = (uintptr_t)r.A, b0 = (uintptr_t)r.B, n = (uintptr_t)(total * es);
+    if (a0 < b0 + n && b0 < a0 + n) return fail(SPINSUM_ERR_ALIAS, "A and B overlap (use inplace = 1 for A == B)");
+  }
+  // page-locked host memory mapped into the device address space: the orbit
+  // kernel reads A and writes B in place over the host link (zero-copy), in
+  // one launch that streams both directions at once
+  {
+    cudaPointerAttributes pa, pb;
+    if (cudaPointerGetAttributes(&pa, r.A) == cudaSuccess && cudaPointerGetAttributes(&pb, r.B) == cudaSuccess &&
+        pa.type == cudaMemoryTypeHost && pb.type == cudaMemoryTypeHost && pa.devicePointer && pb.devicePointer) {
+      Request q = r;
+      q.A = pa.devicePointer;
+      q.B = pb.devicePointer;
+      return run(q, user);
+    }
+    cudaGetLastError();  // clear a sticky "invalid value" from probing pageable memory
+  }
+  if (!ws) return fail(SPINSUM_ERR_ARG, "null workspace");
+  // chunk = a range of the slowest spectator index; three slots, each with the
+  // A chunk (summed in place on the device) and, when beta != 0 out of place,
+  // the B chunk
+  const int64_t slow = r.ext[d - 1];
+  const int64_t inner = dense[d - 1];            // spectator elements per slow index value
+  const int64_t rows = total / (inner * slow);   // permuted tuples
+  const int per_slot = (r.beta != 0.0 && !r.inplace) ? 2 : 1;
+  const int64_t slice_bytes = inner * rows * (int64_t)es * per_slot;
+  int64_t delta = (int64_t)(ws_bytes / 3) / std::max<int64_t>(1, slice_bytes);
+  if (delta < 1) return fail(SPINSUM_ERR_ARG, "workspace too small: at least %lld bytes", (long long)(3 * slice_bytes));
+  delta = std::min(delta, std::max<int64_t>(1, (slow + 7) / 8));   // at least ~8 chunks to overlap
+  const int64_t nchunks = (slow + delta - 1) / delta;
+  const size_t slot_bytes = (size_t)(delta * slice_bytes);
+  HostPipe* P = nullptr;
+  int rc = host_pipe(&P);
+  if (rc != SPINSUM_OK) return rc;
+  while (P->ev.size() < 9) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "creating the pipeline events");
+    P->ev.push_back(ev);
+  }
+  cudaError_t e = cudaEventRecord(P->start, user);
+  for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaStreamWaitEvent(P->s[k], P->start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "ordering after the caller's stream");
+  const unsigned char* hA = static_cast<const unsigned char*>(r.A);
+  unsigned char* hB = static_cast<unsigned char*>(r.B);
+  const size_t pitch = (size_t)(inner * slow) * es;
+  for (int64_t c = 0; c < nchunks; c++) {
+    const int slot = (int)(c % 3);
+    const int64_t c0 = c * delta, dc = std::min(delta, slow - c0);
+    const size_t width = (size_t)(inner * dc) * es;
+    unsigned char* dA = static_cast<unsigned char*>(ws) + slot * slot_bytes;
+    unsigned char* dB = per_slot == 2 ? dA + slot_bytes / 2 : dA;
+    cudaEvent_t ev_in = P->ev[slot * 3], ev_done = P->ev[slot * 3 + 1], ev_free = P->ev[slot * 3 + 2];
+    if (c >= 3 && (e = cudaStreamWaitEvent(P->s[0], ev_free, 0)) != cudaSuccess) break;
+    e = cudaMemcpy2DAsync(dA, width, hA + (size_t)(c0 * inner) * es, pitch, width, (size_t)rows,
+                          cudaMemcpyHostToDevice, P->s[0]);
+    if (e == cudaSuccess && per_slot == 2)
+      e = cudaMemcpy2DAsync(dB, width, hB + (size_t)(c0 * inner) * es, pitch, width, (size_t)rows,
+                            cudaMemcpyHostToDevice, P->s[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, P->s[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s[1], ev_in, 0);
+    if (e != cudaSuccess) break;
+    // the chunk as a dense device tensor: slow spectator extent dc
+    int64_t cext[8], cld[8], s1 = 1;
+    for (int k = 0; k < nidx; k++) {
+      cext[k] = (k == d - 1) ? dc : r.ext[k];
+      cld[k] = s1;
+      s1 *= cext[k];
+    }
+    Request q = r;
+    q.ext = cext;
+    q.lda = cld;
+    q.ldb = cld;
+    q.A = dA;
+    q.B = dB;
+    q.inplace = per_slot == 1;
+    rc = run(q, P->s[1]);
+    if (rc != SPINSUM_OK) return rc;
+    if ((e = cudaEventRecord(ev_done, P->s[1])) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(P->s[2], ev_done, 0)) != cudaSuccess) break;
+    e = cudaMemcpy2DAsync(hB + (size_t)(c0 * inner) * es, pitch, dB, width, width, (size_t)rows,
+                          cudaMemcpyDeviceToHost, P->s[2]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_free, P->s[2]);
+    if (e != cudaSuccess) break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "host pipeline");
+  for (int k = 0; k < 3 && e == cudaSuccess; k++) {
+    e = cudaEventRecord(P->end, P->s[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(user, P->end, 0);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ordering the caller's stream after the pipeline");
+  return SPINSUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spinsum_3d_host(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
+                    const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream) {
+  Request r{3, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run_host(r, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
+                    const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream) {
+  Request r{4, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run_host(r, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // batched plans: problems grouped by (d, arithmetic); each class runs as one
 // persistent launch of the batched kernel over its problems' K1 blocks.
 // Problems whose layout needs the general kernel are launched one by one.
