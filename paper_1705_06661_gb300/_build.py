@@ -1,5 +1,7 @@
 """Build of the CUDA library: nvcc for sm_103a, one object per translation
-unit, compiled in parallel, linked into _build/libspinsum.so (in-tree)."""
+unit, compiled in parallel, linked into _build/libspinsum.so (in-tree).
+SPINSUM_NVCC_FLAGS adds nvcc flags (e.g. -D overrides of the kernel shape
+constants in csrc/ss_internal.h)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -34,7 +36,7 @@ def _commands():
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-               "-I", INCLUDE, "-c", src, "-o", obj]
+               "-I", INCLUDE, *os.environ.get("SPINSUM_NVCC_FLAGS", "").split(), "-c", src, "-o", obj]
         cmds.append((src, obj, cmd, deps))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cpp"))):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")

@@ -145,6 +145,15 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_K1T4_NST 3
 #endif
 
+// 4D generic orbit in the exact core: outputs per register group (24 / G)
+// and the CTAs per SM the kernel is compiled for
+#ifndef SS_4D_GROUPS
+#define SS_4D_GROUPS 4
+#endif
+#ifndef SS_4D_MINBLOCKS
+#define SS_4D_MINBLOCKS 3
+#endif
+
 constexpr int MAXSTAGE = 8;
 constexpr int MAXSTAGE_EXACT = 3;  // the exact core unrolls at most this many stages
 constexpr int MAXSPEC = 4;

@@ -417,7 +417,7 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
         if (beta) v = add_beta(v, *dst, kp.beta);
         *dst = v;
       };
-      if (!exact_core_grouped4<4>(kp, x[0], sink)) strict_fallback_generic4(kp, soff[0], soff[1], s);
+      if (!exact_core_grouped4<SS_4D_GROUPS>(kp, x[0], sink)) strict_fallback_generic4(kp, soff[0], soff[1], s);
       continue;
     }
 #pragma unroll
@@ -479,7 +479,7 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
 }
 
 template <int D, int AR, int VEC, typename T>
-__global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? 3 : 1) k1_kernel(const __grid_constant__ KParams kp) {
+__global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? SS_4D_MINBLOCKS : 1) k1_kernel(const __grid_constant__ KParams kp) {
   k1_block<D, AR, VEC, T>(kp, blockIdx.x);
 }
 
