@@ -21,6 +21,7 @@ namespace ss {
 cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st);
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st);
 int k1t_chunk(int d, int ar);
 
 int* status_ptr();
@@ -427,6 +428,16 @@ int plan_one(const Request& r, Launch* L) {
       for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
     }
     if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
+  } else if (S == 1 && kp.lda[0] == 1 && kp.ldb[0] == 1) {
+    // the paper's layout: no spectators, the first permuted index at stride 1 --
+    // tiled block orbits through shared memory (K2)
+    L->kernel = 3;
+    const int bl = d == 3 ? 8 : 4;
+    const int nb = (O + bl - 1) / bl;
+    kp.pre[0] = 0;
+    for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + binom(nb, nd_of(d, p));
+    for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+    if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
   } else {
     L->kernel = 1;
     kp.gpre[0] = 0;
@@ -446,6 +457,7 @@ int run(const Request& r, cudaStream_t st) {
   L.kp.status = status_ptr();
   cudaError_t e = L.kernel == 0   ? launch_k1(r.d, L.kp, L.ar, L.vec, st)
                   : L.kernel == 2 ? launch_k1t(r.d, L.kp, L.ar, st)
+                  : L.kernel == 3 ? launch_k2(r.d, L.kp, L.ar, st)
                                   : launch_kg(r.d, L.kp, L.ar, st);
   t_launches++;
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -722,7 +734,7 @@ std::vector<ClassRange> fill_batch(const std::vector<Launch>& ls, const std::vec
       ClassRange c{d, ar, next, pnext, 0, 0};
       for (int i : order) {
         const Launch& L = ls[i];
-        if (L.kernel == 1 || L.kp.nspec != d || L.ar != ar) continue;
+        if (L.kernel == 1 || L.kernel == 3 || L.kp.nspec != d || L.ar != ar) continue;
         KParams kp = L.kp;
         kp.status = status;
         const int vec = (L.vec > 1 && !(d == 4 && L.ar == AR_F32)) ? L.vec : 1;
@@ -815,7 +827,7 @@ int plan_launch(spinsum_plan* P, cudaStream_t st) {
   for (int i : P->general) {
     Launch L = P->launches[i];
     L.kp.status = status_ptr();
-    cudaError_t e = launch_kg(L.kp.nspec, L.kp, L.ar, st);
+    cudaError_t e = L.kernel == 3 ? launch_k2(L.kp.nspec, L.kp, L.ar, st) : launch_kg(L.kp.nspec, L.kp, L.ar, st);
     t_launches++;
     if (e != cudaSuccess) return cuda_fail(e, "general kernel launch");
   }
@@ -900,7 +912,7 @@ int spinsum_plan_create(spinsum_plan** plan, const spinsum_problem* problems, in
       return fail(rc, "%s", m.c_str());
     }
     if (L.empty) continue;
-    if (L.kernel == 1) P->general.push_back((int)P->launches.size());
+    if (L.kernel == 1 || L.kernel == 3) P->general.push_back((int)P->launches.size());
     P->launches.push_back(L);
   }
   P->shape = image_shape((int)P->launches.size());
@@ -1038,10 +1050,10 @@ extern "C" int spinsum_batch_static(const spinsum_problem* problems, int nproble
     if (e != cudaSuccess) return cuda_fail(e, "static batched kernel launch");
   }
   for (const Launch& L : launches) {
-    if (L.kernel != 1) continue;
+    if (L.kernel != 1 && L.kernel != 3) continue;
     KParams kp = L.kp;
     kp.status = status_ptr();
-    e = launch_kg(kp.nspec, kp, L.ar, st);
+    e = L.kernel == 3 ? launch_k2(kp.nspec, kp, L.ar, st) : launch_kg(kp.nspec, kp, L.ar, st);
     t_launches++;
     if (e != cudaSuccess) return cuda_fail(e, "general kernel launch");
   }
@@ -1080,7 +1092,7 @@ extern "C" int ss_debug_plan(int d, int O, int V, const double* coef, int nfacto
   int64_t v[32] = {L.ar, kp.W, kp.kdrop, kp.nstage, L.kernel, L.vec, kp.flags, kp.cexp, (int64_t)(kp.emin >> 20),
                    (int64_t)(kp.emax >> 20)};
   for (int p = 0; p < 8; p++) v[10 + p] = kp.norb[p];
-  v[18] = L.kernel == 0 ? kp.pre[npatterns(d)] : (kp.ngroup + 255) / 256;
+  v[18] = L.kernel == 1 ? (kp.ngroup + 255) / 256 : kp.pre[npatterns(d)];
   for (int k = 0; k < 19; k++) info[k] = v[k];
   for (int st = 0; st < MAXSTAGE; st++)
     for (int x = 0; x < 24; x++) ci[st * 24 + x] = kp.ci[st][x];

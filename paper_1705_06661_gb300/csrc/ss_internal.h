@@ -212,7 +212,7 @@ struct alignas(16) KParams {
 struct Launch {
   KParams kp;
   int ar = AR_STRICT;
-  int kernel = 0;  // 0 = K1 (registers), 1 = KG (general strides), 2 = K1T (TMA-staged)
+  int kernel = 0;  // 0 = K1 (registers), 1 = KG (general strides), 2 = K1T (TMA-staged), 3 = K2 (N^d tiles)
   int vec = 1;
   bool empty = false;
 };

@@ -13,6 +13,10 @@ cudaError_t launch_k1_d4_exact(const KParams& kp, cudaStream_t st);
 cudaError_t launch_k1_d4_strict(const KParams& kp, cudaStream_t st);
 cudaError_t launch_k1_d4_f32(const KParams& kp, int vec, cudaStream_t st);
 cudaError_t launch_kg_d3(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k2_d3(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k2_d4_exact(const KParams& kp, cudaStream_t st);
+cudaError_t launch_k2_d4_strict(const KParams& kp, cudaStream_t st);
+cudaError_t launch_k2_d4_f32(const KParams& kp, cudaStream_t st);
 cudaError_t launch_kg_d4(const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k1t_d3(const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_kb_d3(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
@@ -54,6 +58,14 @@ int* status_ptr() {
     ptr[dev] = static_cast<int*>(p);
   }
   return ptr[dev];
+}
+
+// tiled kernel for the paper's N^d layout
+cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st) {
+  if (d == 3) return launch_k2_d3(kp, ar, st);
+  if (ar == AR_EXACT) return launch_k2_d4_exact(kp, st);
+  if (ar == AR_STRICT) return launch_k2_d4_strict(kp, st);
+  return launch_k2_d4_f32(kp, st);
 }
 
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st) {

@@ -222,3 +222,8 @@ def test_launch_shape(lib):
     assert info["kernel"] == 0 and info["vec"] == 1
     _, info, _, _ = debug_plan(lib, 3, 16, 3, wl.table2(1))   # 27 spectators: general kernel
     assert info["kernel"] == 1
+    # the paper's N^d layout (no spectators, first permuted index at stride 1): tiled kernel
+    _, info, _, _ = debug_plan(lib, 3, 344, 1, wl.table2(1))
+    assert info["kernel"] == 3 and info["blocks"] == math.comb(43 + 2, 3)   # 8^3 tiles, 43 per edge
+    _, info, _, _ = debug_plan(lib, 4, 80, 1, wl.table2(5))
+    assert info["kernel"] == 3 and info["blocks"] == math.comb(20 + 3, 4)   # 4^4 tiles, 20 per edge
