@@ -45,6 +45,9 @@ CASES = {
     "3d-small": (3, (24, 24, 24, 16, 16, 16), 1),     # 453 MB per tensor: above L2, one ncu capture
     "4d": (4, (12,) * 8, 5),
     "4d-small": (4, (8, 8, 8, 8, 12, 12, 12, 12), 5),
+    # the paper's own layout: a dense N^d tensor, every index permuted (tiled kernel)
+    "paper-3d": (3, (344,) * 3, 1),
+    "paper-4d": (4, (80,) * 4, 5),
 }
 
 

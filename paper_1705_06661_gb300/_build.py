@@ -1,7 +1,8 @@
 """Build of the CUDA library: nvcc for sm_103a, one object per translation
 unit, compiled in parallel, linked into _build/libspinsum.so (in-tree).
 SPINSUM_NVCC_FLAGS adds nvcc flags (e.g. -D overrides of the kernel shape
-constants in csrc/ss_internal.h)."""
+constants in csrc/ss_internal.h); its -D definitions reach the host sources
+too, which size the grids from the same constants."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -40,8 +41,9 @@ def _commands():
         cmds.append((src, obj, cmd, deps))
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cpp"))):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", _cuda_include(), "-c", src,
-               "-o", obj]
+        defs = [f for f in os.environ.get("SPINSUM_NVCC_FLAGS", "").split() if f.startswith("-D")]
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", _cuda_include(), *defs, "-c",
+               src, "-o", obj]
         cmds.append((src, obj, cmd, deps))
     return cmds
 

@@ -434,10 +434,12 @@ int plan_one(const Request& r, Launch* L) {
     L->kernel = 3;
     const int bl = d == 3 ? 8 : 4;
     const int nb = (O + bl - 1) / bl;
-    kp.pre[0] = 0;
-    for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + binom(nb, nd_of(d, p));
-    for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
-    if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
+    // CTAs in groups of F^d over sorted coarse tuples (multisets of d of nc values)
+    kp.k2lf = d == 3 ? SS_K2_LF3 : SS_K2_LF4;
+    const int64_t nc = ((nb - 1) >> kp.k2lf) + 1;
+    const int64_t grid = binom(nc + d - 1, d) << (d * kp.k2lf);
+    for (int p = 0; p <= 8; p++) kp.pre[p] = p < np ? 0 : grid;
+    if (grid > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
   } else {
     L->kernel = 1;
     kp.gpre[0] = 0;
@@ -1093,7 +1095,8 @@ extern "C" int ss_debug_plan(int d, int O, int V, const double* coef, int nfacto
                    (int64_t)(kp.emax >> 20)};
   for (int p = 0; p < 8; p++) v[10 + p] = kp.norb[p];
   v[18] = L.kernel == 1 ? (kp.ngroup + 255) / 256 : kp.pre[npatterns(d)];
-  for (int k = 0; k < 19; k++) info[k] = v[k];
+  v[19] = L.kernel == 3 ? kp.k2lf : 0;
+  for (int k = 0; k < 20; k++) info[k] = v[k];
   for (int st = 0; st < MAXSTAGE; st++)
     for (int x = 0; x < 24; x++) ci[st * 24 + x] = kp.ci[st][x];
   for (int k = 0; k < MP_MAX; k++) mp[k] = kp.mp[k];

@@ -147,6 +147,26 @@ constexpr int MP_MAX = MP_TOTAL_4;
 
 // 4D generic orbit in the exact core: outputs per register group (24 / G)
 // and the CTAs per SM the kernel is compiled for
+// K2 CTA grouping: log2 of the tiles per coarse-block edge (3D / 4D)
+#ifndef SS_K2_LF3
+#define SS_K2_LF3 1
+#endif
+#ifndef SS_K2_LF4
+#define SS_K2_LF4 2
+#endif
+// K2 launch shape: 0 one CTA per block orbit, 2 persistent CTAs with
+// double-buffered tiles
+#ifndef SS_K2_MODE
+#define SS_K2_MODE 0
+#endif
+// K2 (one orbit per CTA): minimum resident CTAs per SM the register budget is sized for
+#ifndef SS_K2_MINB3
+#define SS_K2_MINB3 5
+#endif
+#ifndef SS_K2_MINB4
+#define SS_K2_MINB4 2
+#endif
+
 #ifndef SS_4D_GROUPS
 #define SS_4D_GROUPS 4
 #endif
@@ -203,6 +223,7 @@ struct alignas(16) KParams {
   int64_t pre[9];
   int64_t nchunk;               // chunks per orbit
   int cpb;                      // chunks per block
+  int k2lf;                     // K2: log2 of the tiles per coarse-block edge (CTA grouping)
   int64_t norb[8];              // orbits per pattern
   int64_t ngroup;               // general kernel: total orbit-element groups
   int64_t gpre[9];              // general kernel: group prefix per pattern

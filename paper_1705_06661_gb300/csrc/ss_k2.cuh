@@ -112,15 +112,14 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
 }
 
 // element pattern of the sorted tuple with adjacent-equality bits eq
+// (d = 3: bit 0 = (0,1), bit 1 = (1,2) equal; d = 4: bits (0,1), (1,2), (2,3)),
+// as a pattern index of ss_internal.h; a packed table, not a local-memory array
 template <int D>
 __device__ __forceinline__ int k2_elem_pattern(unsigned eq) {
   if constexpr (D == 3) {
-    constexpr int t[4] = {0, 1, 2, 3};  // bits: 1 = (0,1) equal, 2 = (1,2) equal
-    return t[eq];
+    return (int)eq;
   } else {
-    // bits 1 = (0,1), 2 = (1,2), 4 = (2,3) -> pattern index of ss_internal.h
-    constexpr int t[8] = {0, 1, 2, 5, 3, 4, 6, 7};
-    return t[eq];
+    return (int)((0x76435210u >> (4 * eq)) & 0xFu);  // eq 0..7 -> 0 1 2 5 3 4 6 7
   }
 }
 
@@ -143,56 +142,276 @@ __device__ __forceinline__ void k2_dispatch(const KParams& kp, int ep, const int
   }
 }
 
-template <int D, int BP, int AR, typename T>
-__device__ __forceinline__ void k2_body(const KParams& kp, int64_t orb, T* sm) {
+// asynchronous global -> shared copies (cp.async, completion by commit groups)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One block orbit as the CTA sees it: the sorted block tuple (pattern bp,
+// distinct values val), and per tile member u its A and B origins, its extent
+// left before the upper edge of the tensor per dimension, and whether it is a
+// full tile. bp < 0 marks the end of the CTA's list.
+struct K2Desc {
+  int64_t base[2][24];
+  int lim[24][4];
+  unsigned char full[24];
+  int64_t id;
+  int bp, mb;
+  int val[4];
+};
+
+// lanes u < m_b of one warp fill the tile table of a block orbit of pattern BP
+template <int D, int BP>
+__device__ __forceinline__ void k2_fill(const KParams& kp, const int (&val)[4], K2Desc& dsc) {
   using K = K2Shape<D>;
   constexpr int MB = Pat<D, BP>::M;
-  const int N = kp.O;
-  const int nb = (N + K::BL - 1) / K::BL;
-  int val[4] = {0, 0, 0, 0};
-  unrank<Pat<D, BP>::ND>(orb, nb, val);
-  const T* A = static_cast<const T*>(kp.A);
-  T* B = static_cast<T*>(kp.B);
-  // block coordinates and origins (A and B element offsets) of the m_b tiles
-  __shared__ int sblk[24][4];
-  __shared__ int64_t sbase[2][24];
-  __syncthreads();
-  if (threadIdx.x < MB) {
-    const int u = threadIdx.x;
+  const int u = threadIdx.x & 31;
+  if (u == 0) {
+    dsc.bp = BP;
+    dsc.mb = MB;
+  }
+  if (u < D) dsc.val[u] = u == 0 ? val[0] : (u == 1 ? val[1] : (u == 2 ? val[2] : val[3]));
+  if (u < MB) {
     int64_t oa = 0, ob = 0;
+    bool full = true;
 #pragma unroll
     for (int k = 0; k < D; k++) {
-      const int bk = val[kPattern<D, BP>.lab[u][k]];
-      sblk[u][k] = bk;
+      const int l = kPattern<D, BP>.lab[u][k];  // selects, not a local-memory index
+      const int bk = l == 0 ? val[0] : (l == 1 ? val[1] : (l == 2 ? val[2] : val[3]));
+      dsc.lim[u][k] = kp.O - bk * K::BL;
+      full = full && kp.O - bk * K::BL >= K::BL;
       oa += (int64_t)bk * K::BL * kp.lda[k];
       ob += (int64_t)bk * K::BL * kp.ldb[k];
     }
-    sbase[0][u] = oa;
-    sbase[1][u] = ob;
+    dsc.base[0][u] = oa;
+    dsc.base[1][u] = ob;
+    dsc.full[u] = full;
   }
-  __syncthreads();
-  // 1. tiles -> shared memory
-  for (int i = threadIdx.x; i < MB * K::NT; i += blockDim.x) {
-    const int u = i / K::NT;
-    int e = i - u * K::NT;
-    int64_t off = sbase[0][u];
-    int slot = u * K::TS;
-    bool in = true;
+}
+
+// Colex unranking as in unrank(), by a whole warp at once: the candidates c of
+// each position are tested 32 at a time (C(c, i + 1) grows with c, so the
+// qualifying c form a prefix and the answer is its last element). Every lane
+// returns the same tuple; all 32 lanes must be active.
+template <int ND>
+__device__ __forceinline__ void unrank_warp(int64_t r, int O, int (&v)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = ND - 1; i >= 0; i--) {
+    int cnt = 0;
+    for (int c0 = i; c0 < O; c0 += 32) {
+      const int c = c0 + lane;
+      const unsigned m = __ballot_sync(0xffffffffu, c < O && binom(c, i + 1) <= r);
+      cnt += __popc(m);
+      if (m != 0xffffffffu) break;
+    }
+    v[i] = i + cnt - 1;
+    r -= binom(v[i], i + 1);
+  }
+}
+
+// Work ids and block orbits. Block orbits are visited in groups: the sorted
+// tuple c of coarse blocks (F tiles per edge, F = 2^k2lf) is unranked from
+// id / F^d as a multiset (colex rank of the strictly increasing c_k + k), and
+// the F^d consecutive ids of the group take the fine tuples b_k = F c_k +
+// delta_k. Sorted fine tuples need delta non-decreasing where c repeats; the
+// other ids of a group are skipped. CTAs take ids id0, id0 + G, ... (G CTAs
+// in the grid), so the ids in flight at any time form a window of consecutive
+// groups: every tile row of the F^d tiles of a coarse tile (F x BL x
+// sizeof(T) contiguous bytes) is read and written at about the same time.
+// One whole warp finds the first valid id >= id0 (step G) and fills dsc.
+template <int D>
+__device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t step, K2Desc& dsc) {
+  const int lf = kp.k2lf;
+  const int nb = (kp.O + K2Shape<D>::BL - 1) / K2Shape<D>::BL;
+  const int nc = ((nb - 1) >> lf) + 1;
+  const int64_t total = kp.pre[npatterns(D)];
+  const int fm = (1 << lf) - 1;
+  for (; id < total; id += step) {
+    int v[4] = {0, 0, 0, 0};
+    unrank_warp<D>(id >> (D * lf), nc + D - 1, v);
+    const unsigned dl = (unsigned)id & ((1u << (D * lf)) - 1u);
+    int b[4] = {0, 0, 0, 0};
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < D; k++) {
-      const int wk = e % K::BL;
-      e /= K::BL;
-      in = in && sblk[u][k] * K::BL + wk < N;
-      off += (int64_t)wk * kp.lda[k];
-      slot += wk * K::pitch(k);
+      b[k] = ((v[k] - k) << lf) + (int)((dl >> (k * lf)) & fm);
+      ok = ok && b[k] < nb;
     }
-    if (in) sm[slot] = A[off];
+    unsigned eq = 0;
+    int val[4] = {b[0], 0, 0, 0};
+    int j = 0;
+#pragma unroll
+    for (int k = 0; k + 1 < D; k++) {
+      ok = ok && b[k] <= b[k + 1];
+      if (b[k] == b[k + 1]) {
+        eq |= 1u << k;
+      } else {
+        j++;
+        if (j == 1) val[1] = b[k + 1];
+        if (j == 2) val[2] = b[k + 1];
+        if (j == 3) val[3] = b[k + 1];
+      }
+    }
+    if (!ok) continue;
+    if ((threadIdx.x & 31) == 0) dsc.id = id;
+    switch (k2_elem_pattern<D>(eq)) {
+      case 0: k2_fill<D, 0>(kp, val, dsc); break;
+      case 1: k2_fill<D, 1>(kp, val, dsc); break;
+      case 2: k2_fill<D, 2>(kp, val, dsc); break;
+      case 3: k2_fill<D, 3>(kp, val, dsc); break;
+      default:
+        if constexpr (D == 4) {
+          switch (k2_elem_pattern<D>(eq)) {
+            case 4: k2_fill<D, 4>(kp, val, dsc); break;
+            case 5: k2_fill<D, 5>(kp, val, dsc); break;
+            case 6: k2_fill<D, 6>(kp, val, dsc); break;
+            case 7: k2_fill<D, 7>(kp, val, dsc); break;
+          }
+        }
+    }
+    return;
   }
-  __syncthreads();
-  // 2. element orbits of the block orbit, in shared memory
+  if ((threadIdx.x & 31) == 0) dsc.bp = -1;
+}
+
+// Copy the m_b tiles of a block orbit between HBM and shared memory. Each
+// thread owns a fixed run of VEC elements along the stride-1 index at the same
+// in-tile place of every tile (its in-tile offset, shared-memory slot and
+// global offset relative to the tile origin are computed once); per tile it
+// adds the tile's origin and checks the tile's bounds only at the upper edge.
+// LOAD: copies into shared memory, asynchronous with ASYNC (the caller
+// commits and waits), else through registers with 16-byte global loads; store: shared memory -> HBM with the beta term, 16-byte global accesses
+// where the layout allows them.
+template <int D, int VEC, bool LOAD, bool ASYNC, int MBC, typename T>
+__device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& dsc) {
+  using K = K2Shape<D>;
+  constexpr int CPR = K::BL / VEC;          // vector chunks per tile row
+  constexpr int CPT = K::NT / VEC;          // chunks per tile
+  // either several tiles per pass of 256 threads, or several chunks of one tile per thread
+  constexpr int TPP = CPT <= 256 ? 256 / CPT : 1;
+  constexpr int NCH = CPT <= 256 ? 1 : CPT / 256;
+  static_assert(CPT <= 256 ? 256 % CPT == 0 : CPT % 256 == 0, "tile chunks must tile the block");
+  const int64_t* ld = LOAD ? kp.lda : kp.ldb;
+  const int64_t* base = dsc.base[LOAD ? 0 : 1];
+  const int mb = MBC > 0 ? MBC : dsc.mb;
+  const int u0 = CPT <= 256 ? threadIdx.x / CPT : 0;
+  int w[NCH][4];
+  int64_t goff[NCH];
+  int slot[NCH];
+#pragma unroll
+  for (int q = 0; q < NCH; q++) {
+    const int c = (CPT <= 256 ? threadIdx.x % CPT : threadIdx.x) + q * 256;
+    w[q][0] = (c % CPR) * VEC;
+    int r = c / CPR;
+#pragma unroll
+    for (int k = 1; k < 4; k++) {
+      w[q][k] = 0;
+      if (k < D) {
+        w[q][k] = r % K::BL;
+        r /= K::BL;
+      }
+    }
+    goff[q] = 0;
+    slot[q] = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+      goff[q] += (int64_t)w[q][k] * ld[k];
+      slot[q] += w[q][k] * K::pitch(k);
+    }
+  }
+  T* G = LOAD ? const_cast<T*>(static_cast<const T*>(kp.A)) : static_cast<T*>(kp.B);
+  if constexpr (LOAD && !ASYNC && MBC > 0) {
+    // every load of the thread first (all in flight together), then the
+    // shared-memory writes
+    constexpr int NIT = (MBC + TPP - 1) / TPP;
+    T v[NIT][NCH][VEC];
+    unsigned inb = 0;
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+      const int u = u0 + it * TPP;
+      if (NIT * TPP != MBC && u >= MBC) continue;
+      const bool full_u = dsc.full[u];
+#pragma unroll
+      for (int q = 0; q < NCH; q++) {
+        bool in = full_u;
+        if (!in) {
+          in = true;
+#pragma unroll
+          for (int k = 0; k < D; k++) in = in && w[q][k] < dsc.lim[u][k];
+        }
+        if (in) {
+          inb |= 1u << (it * NCH + q);
+          vload<T, VEC>(G + base[u] + goff[q], v[it][q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; it++) {
+      const int u = u0 + it * TPP;
+#pragma unroll
+      for (int q = 0; q < NCH; q++) {
+        if (!(inb >> (it * NCH + q) & 1u)) continue;
+        T* sp = sm + u * K::TS + slot[q];
+#pragma unroll
+        for (int i = 0; i < VEC; i++) sp[i] = v[it][q][i];
+      }
+    }
+    return;
+  }
+  const bool beta = !LOAD && (kp.flags & KF_BETA);
+  const T bt = beta_of<T>(kp);
+  for (int u = u0; u < mb; u += TPP) {
+    const bool full_u = dsc.full[u];
+#pragma unroll
+    for (int q = 0; q < NCH; q++) {
+      bool in = full_u;
+      if (!in) {
+        in = true;
+#pragma unroll
+        for (int k = 0; k < D; k++) in = in && w[q][k] < dsc.lim[u][k];
+      }
+      if (!in) continue;
+      T* g = G + base[u] + goff[q];
+      T* sp = sm + u * K::TS + slot[q];
+      if constexpr (LOAD && ASYNC) {
+        // the padded slots are not 16-byte aligned: element-sized copies
+#pragma unroll
+        for (int i = 0; i < VEC; i++) cp_async<sizeof(T)>(sp + i, g + i);
+      } else if constexpr (LOAD) {
+        T v[VEC];
+        vload<T, VEC>(g, v);
+#pragma unroll
+        for (int i = 0; i < VEC; i++) sp[i] = v[i];
+      } else {
+        T v[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC; i++) v[i] = sp[i];
+        if (beta) {
+          T o[VEC];
+          vload<T, VEC>(g, o);
+#pragma unroll
+          for (int i = 0; i < VEC; i++) v[i] = add_beta(v[i], o[i], bt);
+        }
+        vstore<T, VEC>(g, v);
+      }
+    }
+  }
+}
+
+// the element orbits of one block orbit of pattern BP, in shared memory: each
+// thread takes canonical in-tile offsets w of the first tile member
+template <int D, int BP, int AR, typename T>
+__device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, T* sm) {
+  using K = K2Shape<D>;
   int T0[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int k = 0; k < D; k++) T0[k] = val[Pat<D, BP>::lab(0, k)];
+  for (int k = 0; k < D; k++) T0[k] = dsc.val[Pat<D, BP>::lab(0, k)];
   for (int e0 = threadIdx.x; e0 < K::NT; e0 += blockDim.x) {
     int w[4] = {0, 0, 0, 0};
     int e = e0;
@@ -201,7 +420,7 @@ __device__ __forceinline__ void k2_body(const KParams& kp, int64_t orb, T* sm) {
       w[k] = e % K::BL;
       e /= K::BL;
     }
-    bool ok = T0[D - 1] * K::BL + w[D - 1] < N;  // the largest coordinate of the sorted tuple
+    bool ok = T0[D - 1] * K::BL + w[D - 1] < kp.O;  // the largest coordinate of the sorted tuple
     unsigned eq = 0;
 #pragma unroll
     for (int k = 0; k + 1 < D; k++) {
@@ -213,73 +432,160 @@ __device__ __forceinline__ void k2_body(const KParams& kp, int64_t orb, T* sm) {
     if (!ok) continue;
     k2_dispatch<D, BP, AR, T>(kp, k2_elem_pattern<D>(eq), w, sm);
   }
-  __syncthreads();
-  // 3. shared memory -> tiles (alpha applied; beta added here)
-  const bool beta = kp.flags & KF_BETA;
-  const T bt = beta_of<T>(kp);
-  for (int i = threadIdx.x; i < MB * K::NT; i += blockDim.x) {
-    const int u = i / K::NT;
-    int e = i - u * K::NT;
-    int64_t off = sbase[1][u];
-    int slot = u * K::TS;
-    bool in = true;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      const int wk = e % K::BL;
-      e /= K::BL;
-      in = in && sblk[u][k] * K::BL + wk < N;
-      off += (int64_t)wk * kp.ldb[k];
-      slot += wk * K::pitch(k);
-    }
-    if (in) {
-      T v = sm[slot];
-      if (beta) v = add_beta(v, B[off], bt);
-      B[off] = v;
-    }
-  }
 }
 
 template <int D, int AR, typename T>
-__global__ void __launch_bounds__(256) k2_kernel(const __grid_constant__ KParams kp) {
-  extern __shared__ __align__(16) unsigned char k2_smem[];
-  T* sm = reinterpret_cast<T*>(k2_smem);
-  const int64_t b = blockIdx.x;
-  const int p = find_pattern<D>(kp.pre, b);
-  const int64_t orb = b - kp.pre[p];
-  switch (p) {
-    case 0: k2_body<D, 0, AR, T>(kp, orb, sm); break;
-    case 1: k2_body<D, 1, AR, T>(kp, orb, sm); break;
-    case 2: k2_body<D, 2, AR, T>(kp, orb, sm); break;
-    case 3: k2_body<D, 3, AR, T>(kp, orb, sm); break;
+__device__ __forceinline__ void k2_compute(const KParams& kp, const K2Desc& dsc, T* sm) {
+  switch (dsc.bp) {
+    case 0: k2_orbits<D, 0, AR, T>(kp, dsc, sm); break;
+    case 1: k2_orbits<D, 1, AR, T>(kp, dsc, sm); break;
+    case 2: k2_orbits<D, 2, AR, T>(kp, dsc, sm); break;
+    case 3: k2_orbits<D, 3, AR, T>(kp, dsc, sm); break;
     default:
       if constexpr (D == 4) {
-        switch (p) {
-          case 4: k2_body<D, 4, AR, T>(kp, orb, sm); break;
-          case 5: k2_body<D, 5, AR, T>(kp, orb, sm); break;
-          case 6: k2_body<D, 6, AR, T>(kp, orb, sm); break;
-          case 7: k2_body<D, 7, AR, T>(kp, orb, sm); break;
+        switch (dsc.bp) {
+          case 4: k2_orbits<D, 4, AR, T>(kp, dsc, sm); break;
+          case 5: k2_orbits<D, 5, AR, T>(kp, dsc, sm); break;
+          case 6: k2_orbits<D, 6, AR, T>(kp, dsc, sm); break;
+          case 7: k2_orbits<D, 7, AR, T>(kp, dsc, sm); break;
         }
       }
   }
 }
 
-template <int D, int AR, typename T>
-cudaError_t launch_k2_impl(const KParams& kp, cudaStream_t st) {
-  constexpr size_t smem = (size_t)fact(D) * K2Shape<D>::TS * sizeof(T);
-  auto fn = k2_kernel<D, AR, T>;
+// One block orbit per CTA (SS_K2_MODE 0): the tile table is filled by warp 0,
+// the phases run with the member count m_b a compile-time constant.
+template <int D, int BP, int AR, int VEC, typename T>
+__device__ __forceinline__ void k2_one(const KParams& kp, const K2Desc& dsc, T* sm) {
+  constexpr int MB = Pat<D, BP>::M;
+  k2_copy<D, VEC, true, false, MB, T>(kp, sm, dsc);
+  __syncthreads();
+  k2_orbits<D, BP, AR, T>(kp, dsc, sm);
+  __syncthreads();
+  k2_copy<D, VEC, false, false, MB, T>(kp, sm, dsc);
+}
+
+template <int D, int AR, int VEC, typename T>
+__global__ void __launch_bounds__(256, D == 4 ? SS_K2_MINB4 : SS_K2_MINB3) k2_kernel1(const __grid_constant__ KParams kp) {
+  extern __shared__ __align__(16) unsigned char k2_smem[];
+  T* const sm = reinterpret_cast<T*>(k2_smem);
+  __shared__ K2Desc dsc;
+  if (threadIdx.x < 32) k2_next<D>(kp, blockIdx.x, kp.pre[npatterns(D)], dsc);  // this id only
+  __syncthreads();
+  switch (dsc.bp) {
+    case 0: k2_one<D, 0, AR, VEC, T>(kp, dsc, sm); break;
+    case 1: k2_one<D, 1, AR, VEC, T>(kp, dsc, sm); break;
+    case 2: k2_one<D, 2, AR, VEC, T>(kp, dsc, sm); break;
+    case 3: k2_one<D, 3, AR, VEC, T>(kp, dsc, sm); break;
+    default:
+      if constexpr (D == 4) {
+        switch (dsc.bp) {
+          case 4: k2_one<D, 4, AR, VEC, T>(kp, dsc, sm); break;
+          case 5: k2_one<D, 5, AR, VEC, T>(kp, dsc, sm); break;
+          case 6: k2_one<D, 6, AR, VEC, T>(kp, dsc, sm); break;
+          case 7: k2_one<D, 7, AR, VEC, T>(kp, dsc, sm); break;
+        }
+      }
+  }
+}
+
+// CTAs over the block orbits of their id list (one id each when the grid
+// covers all ids). With NBUF = 2 (persistent CTAs) the tiles of the next block
+// orbit are copied asynchronously into the second buffer while the current
+// one is computed and stored back; with NBUF = 1 the phases follow one
+// another. Block orbits own disjoint tiles, so in place the prefetch of
+// the next orbit never reads an element the current one writes. The tile
+// tables rotate through three slots: the one being filled for the next orbit
+// is neither the current one nor the one the previous orbit's stores may
+// still be reading.
+template <int D, int AR, int VEC, int NBUF, typename T>
+__global__ void __launch_bounds__(256, D == 4 ? 2 : 1) k2_kernel(const __grid_constant__ KParams kp) {
+  using K = K2Shape<D>;
+  extern __shared__ __align__(16) unsigned char k2_smem[];
+  T* const buf0 = reinterpret_cast<T*>(k2_smem);
+  T* const buf1 = buf0 + (NBUF > 1 ? fact(D) * K::TS : 0);
+  __shared__ K2Desc dsc[3];
+  const bool w0 = threadIdx.x < 32;
+  if (w0) k2_next<D>(kp, blockIdx.x, gridDim.x, dsc[0]);
+  __syncthreads();
+  if (dsc[0].bp < 0) return;
+  if constexpr (NBUF > 1) {
+    k2_copy<D, VEC, true, true, 0, T>(kp, buf0, dsc[0]);
+    cp_async_commit();
+  }
+  for (int k = 0;; k++) {
+    const K2Desc& cur = dsc[k % 3];
+    K2Desc& nxt = dsc[(k + 1) % 3];
+    T* const cb = (k & 1) ? buf1 : buf0;
+    if constexpr (NBUF > 1) {
+      if (w0) k2_next<D>(kp, cur.id + gridDim.x, gridDim.x, nxt);
+      __syncthreads();  // nxt ready; the previous orbit's stores from the other buffer are done
+      if (nxt.bp >= 0) k2_copy<D, VEC, true, true, 0, T>(kp, (k & 1) ? buf0 : buf1, nxt);
+      cp_async_commit();
+      cp_async_wait<1>();  // this thread's copies of the current orbit have landed
+    } else {
+      k2_copy<D, VEC, true, false, 0, T>(kp, cb, cur);
+    }
+    __syncthreads();
+    k2_compute<D, AR, T>(kp, cur, cb);
+    __syncthreads();
+    k2_copy<D, VEC, false, false, 0, T>(kp, cb, cur);
+    if constexpr (NBUF == 1) {
+      if (w0) k2_next<D>(kp, cur.id + gridDim.x, gridDim.x, nxt);
+      __syncthreads();  // nxt ready; the buffer is free again
+    }
+    if (nxt.bp < 0) break;
+  }
+}
+
+// Launch shapes (SS_K2_MODE): 0 = one CTA per id (k2_kernel1); 2 =
+// persistent CTAs with two buffers (k2_kernel), where two buffers leave room
+// for more than one CTA per SM.
+template <int D, typename T>
+constexpr int k2_nbuf() {
+  return SS_K2_MODE == 2 && 2 * (size_t)fact(D) * K2Shape<D>::TS * sizeof(T) <= 100 * 1024 ? 2 : 1;
+}
+
+template <int D, int AR, int VEC, typename T>
+cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
+  constexpr int NBUF = k2_nbuf<D, T>();
+  constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::TS * sizeof(T);
+  auto fn = NBUF == 2 ? k2_kernel<D, AR, VEC, 2, T> : k2_kernel1<D, AR, VEC, T>;
   constexpr int MAXDEV = 64;
-  static bool init[MAXDEV] = {false};
+  static int ctas[MAXDEV] = {0};  // resident CTAs per device (persistent grid)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
-  if (!init[dev]) {
+  if (ctas[dev] == 0) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    init[dev] = true;
+    // all of the unified L1/shared array as shared memory: occupancy is set by the tiles
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    ctas[dev] = per_sm * sms;
   }
-  fn<<<(unsigned)kp.pre[npatterns(D)], 256, smem, st>>>(kp);
+  const int64_t ids = kp.pre[npatterns(D)];
+  if (ids == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(NBUF == 2 && ids > ctas[dev] ? ctas[dev] : ids);
+  fn<<<grid, 256, smem, st>>>(kp);
   return cudaGetLastError();
+}
+
+// 16-byte runs along the stride-1 index when the tensor allows them
+template <int D, int AR, typename T>
+cudaError_t launch_k2_impl(const KParams& kp, cudaStream_t st) {
+  constexpr int V = 16 / sizeof(T);
+  bool vec = (kp.O % V == 0) && ((uintptr_t)kp.A % 16 == 0) && ((uintptr_t)kp.B % 16 == 0);
+  for (int k = 1; k < D; k++) vec = vec && (kp.lda[k] % V == 0) && (kp.ldb[k] % V == 0);
+  if (vec) return launch_k2_vec<D, AR, V, T>(kp, st);
+  return launch_k2_vec<D, AR, 1, T>(kp, st);
 }
 
 }  // namespace ss

@@ -135,6 +135,7 @@ def debug_plan(lib, d, O, V, coef, mode=0, alpha=1.0, beta=0.0):
     out = dict(zip(keys, info[:10].tolist()))
     out["norb"] = info[10:18].tolist()
     out["blocks"] = int(info[18])
+    out["k2lf"] = int(info[19])
     return ex, out, ci.reshape(8, 24), mp
 
 
@@ -223,7 +224,9 @@ def test_launch_shape(lib):
     _, info, _, _ = debug_plan(lib, 3, 16, 3, wl.table2(1))   # 27 spectators: general kernel
     assert info["kernel"] == 1
     # the paper's N^d layout (no spectators, first permuted index at stride 1): tiled kernel
-    _, info, _, _ = debug_plan(lib, 3, 344, 1, wl.table2(1))
-    assert info["kernel"] == 3 and info["blocks"] == math.comb(43 + 2, 3)   # 8^3 tiles, 43 per edge
-    _, info, _, _ = debug_plan(lib, 4, 80, 1, wl.table2(5))
-    assert info["kernel"] == 3 and info["blocks"] == math.comb(20 + 3, 4)   # 4^4 tiles, 20 per edge
+    # CTAs: F^d per sorted tuple of coarse blocks (F tiles per coarse edge)
+    for d, N, bl in ((3, 344, 8), (4, 80, 4)):
+        _, info, _, _ = debug_plan(lib, d, N, 1, wl.table2(1 if d == 3 else 5))
+        F = 1 << info["k2lf"]
+        nc = -(-(-(-N // bl)) // F)
+        assert info["kernel"] == 3 and info["blocks"] == math.comb(nc + d - 1, d) * F ** d
