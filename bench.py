@@ -470,6 +470,28 @@ def run_ours(args):
                           "ms_single_launch": round(one * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
         del A4, B4
         torch.cuda.empty_cache()
+        # the paper's own layout: a dense N^d tensor with every index permuted (tiled kernel)
+        for dp, Np, rowp in ((3, 544, 1), (4, 112, 5)):
+            shp = (Np,) * dp
+            Ap = ss.colmajor_empty(shp, device=dev)
+            Ap.copy_(torch.from_numpy(wl.uniform(3, shp)).to(dev))
+            Bp = ss.colmajor_like(Ap)
+            cp = wl.table2(rowp)
+            for name, kw, tgt in [(f"paper layout {dp}d N={Np} row{rowp} factorized out-of-place", {}, Bp),
+                                  (f"paper layout {dp}d N={Np} row{rowp} factorized in-place (alpha=2^-6)",
+                                   {"inplace": True, "alpha": 2.0 ** -6}, None)]:
+                if tgt is None:
+                    fn = lambda cp=cp, kw=kw: ss.spinsum(Ap, cp, d=dp, factorized=True, **kw)  # noqa: E731
+                else:
+                    fn = lambda cp=cp: ss.spinsum(Ap, cp, d=dp, out=Bp, factorized=True)  # noqa: E731
+                for _ in range(2):
+                    fn()
+                mn, one = best_of(fn, reps, stream)
+                npe = Ap.numel()
+                extra.append({"case": name, "GB/s": round(2 * npe * 8 / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                              "frac": round(2 * npe * 8 / mn / 1e9 / hbm_peak, 4)})
+            del Ap, Bp
+            torch.cuda.empty_cache()
         extra += extra_cases_batched_and_autograd(ss, wl, dev, stream, hbm_peak)
         ss.spinsum_check_status(stream.cuda_stream)
 

@@ -154,14 +154,26 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_K2_LF4
 #define SS_K2_LF4 2
 #endif
-// K2 launch shape: 0 one CTA per block orbit, 2 persistent CTAs with
-// double-buffered tiles
-#ifndef SS_K2_MODE
-#define SS_K2_MODE 0
+// K2: buffers of d! tiles per CTA (2 = the next block orbit is copied while the
+// current one is computed) and resident CTAs per SM the register budget is
+// sized for
+#ifndef SS_K2_NBUF3
+#define SS_K2_NBUF3 2
 #endif
-// K2 (one orbit per CTA): minimum resident CTAs per SM the register budget is sized for
+#ifndef SS_K2_NBUF4
+#define SS_K2_NBUF4 1
+#endif
+// K2: consecutive work ids per CTA (0 = persistent grid of the resident CTAs
+// taking every G-th id). Hardware dispatches CTAs in order, so runs keep the
+// ids in flight a compact window; a persistent round robin lets it spread.
+#ifndef SS_K2_RUN3
+#define SS_K2_RUN3 4
+#endif
+#ifndef SS_K2_RUN4
+#define SS_K2_RUN4 1
+#endif
 #ifndef SS_K2_MINB3
-#define SS_K2_MINB3 5
+#define SS_K2_MINB3 4
 #endif
 #ifndef SS_K2_MINB4
 #define SS_K2_MINB4 2

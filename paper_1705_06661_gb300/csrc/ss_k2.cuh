@@ -7,10 +7,10 @@
 // tuple of block coordinates T0 the tiles T0 o tau hold, between them, every
 // element orbit whose block coordinates are a rearrangement of T0 -- the
 // d! blocks of Algorithm 5's macro-kernel (Sec. 4.5), all kept on chip at once.
-// A CTA takes one block orbit:
-//   1. copies its m_b <= d! tiles from HBM into shared memory (rows along the
-//      stride-1 index, coalesced), with padded pitches so that the permuted
-//      reads of step 2 hit few shared-memory banks;
+// A CTA works through block orbits:
+//   1. copies the m_b <= d! tiles of a block orbit from HBM into shared memory
+//      (rows along the stride-1 index, coalesced 16-byte copies; asynchronous,
+//      one block orbit ahead of the one being computed);
 //   2. each thread takes canonical in-tile offsets w of the first tile; the
 //      element orbit of T0 * BL + w has its members in the tiles T0 o tau at
 //      the permuted offsets w o tau (the renaming of Sec. 4.6.1, done per
@@ -19,6 +19,12 @@
 //      the same shared-memory places (each place belongs to one orbit);
 //   3. copies the tiles back to HBM (in place: the same addresses, after every
 //      read of the block orbit is done).
+// Tiles are stored densely in shared memory with an XOR swizzle of the 16-byte
+// unit within each row (and, for d = 4, of the row within each 128-byte line),
+// chosen so that the permuted reads of step 2 -- a warp takes a 4x4x2 (d = 3)
+// or 4x2x2x2 (d = 4) block of canonical offsets -- touch every shared-memory
+// bank equally for all d! permutations, while the copies of steps 1 and 3 keep
+// 16-byte units whole.
 // Partial tiles at the upper edge (N not a multiple of BL) are handled by
 // bounds checks: an element orbit lies entirely inside or outside the tensor.
 #pragma once
@@ -31,14 +37,40 @@ struct K2Shape;
 template <>
 struct K2Shape<3> {
   static constexpr int BL = 8, NT = 512;  // tile edge, elements per tile
-  static constexpr int TS = 608;          // shared-memory slots per tile (padded)
-  __device__ static constexpr int pitch(int k) { return k == 0 ? 1 : (k == 1 ? 9 : 76); }
+  // shared-memory place of in-tile offset c: the pair index c0 / 2 is XORed
+  // with (c1 ^ c2) mod 4
+  __device__ static __forceinline__ int phys(const int (&c)[4]) {
+    return ((((c[0] >> 1) ^ ((c[1] ^ c[2]) & 3)) << 1) | (c[0] & 1)) + 8 * c[1] + 64 * c[2];
+  }
+  // canonical offsets of element e (0..511): warp e / 32 takes the 4x4x2 block
+  // ((e >> 5) & 1, (e >> 6) & 1, e >> 7) of the tile, lane l its element
+  // (l & 3, (l >> 2) & 3, l >> 4)
+  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+    const int l = e & 31, b = e >> 5;
+    w[0] = (l & 3) + 4 * (b & 1);
+    w[1] = ((l >> 2) & 3) + 4 * ((b >> 1) & 1);
+    w[2] = (l >> 4) + 2 * (b >> 2);
+    w[3] = 0;
+  }
 };
 template <>
 struct K2Shape<4> {
   static constexpr int BL = 4, NT = 256;
-  static constexpr int TS = 344;
-  __device__ static constexpr int pitch(int k) { return k == 0 ? 1 : (k == 1 ? 4 : (k == 2 ? 21 : 87)); }
+  // pair bit c0 / 2 XORed with c1.0 ^ c3.0, row c1 XORed with
+  // (c3.1, c2.0 ^ c2.1 ^ c3.1)
+  __device__ static __forceinline__ int phys(const int (&c)[4]) {
+    const int x = c[0] ^ (((c[1] ^ c[3]) & 1) << 1);
+    const int g = (c[3] >> 1) | ((((c[2] ^ (c[2] >> 1)) ^ (c[3] >> 1)) & 1) << 1);
+    return x + 4 * (c[1] ^ g) + 16 * c[2] + 64 * c[3];
+  }
+  // warp e / 32 takes the 4x2x2x2 block (0, b & 1, (b >> 1) & 1, b >> 2) * 2
+  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+    const int l = e & 31, b = e >> 5;
+    w[0] = l & 3;
+    w[1] = ((l >> 2) & 1) + 2 * (b & 1);
+    w[2] = ((l >> 3) & 1) + 2 * ((b >> 1) & 1);
+    w[3] = (l >> 4) + 2 * (b >> 2);
+  }
 };
 
 // For a block pattern BP and an element pattern EP (of a canonical element in
@@ -84,30 +116,33 @@ __device__ constexpr K2Map<D> kK2Map = make_k2map<D>(BP, EP);
 // shared-memory slot of member u of an (BP, EP) element orbit at canonical offset w
 template <int D, int BP, int EP>
 __device__ __forceinline__ int k2_slot(int u, const int (&w)[4]) {
-  int a = kK2Map<D, BP, EP>.bm[u] * K2Shape<D>::TS;
+  int c[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int k = 0; k < D; k++) a += w[kK2Map<D, BP, EP>.tau[u][k]] * K2Shape<D>::pitch(k);
-  return a;
+  for (int k = 0; k < D; k++) c[k] = w[kK2Map<D, BP, EP>.tau[u][k]];
+  return kK2Map<D, BP, EP>.bm[u] * K2Shape<D>::NT + K2Shape<D>::phys(c);
 }
 
 template <int D, int BP, int EP, int AR, typename T>
 __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T* sm) {
   constexpr int M = Pat<D, EP>::M;
+  int s[M];
+#pragma unroll
+  for (int u = 0; u < M; u++) s[u] = k2_slot<D, BP, EP>(u, w);
   T x[M];
 #pragma unroll
-  for (int u = 0; u < M; u++) x[u] = sm[k2_slot<D, BP, EP>(u, w)];
+  for (int u = 0; u < M; u++) x[u] = sm[s[u]];
   if constexpr (D == 4 && EP == 0 && AR == AR_EXACT) {
     const bool amul = kp.flags & KF_ALPHA_MUL;
-    auto sink = [&](int u, double v) { sm[k2_slot<D, BP, EP>(u, w)] = amul ? __dmul_rn(kp.alpha, v) : v; };
+    auto sink = [&](int u, double v) { sm[s[u]] = amul ? __dmul_rn(kp.alpha, v) : v; };
     if (exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) return;
     strict_core<D, EP>(kp, x);
 #pragma unroll
-    for (int u = 0; u < M; u++) sm[k2_slot<D, BP, EP>(u, w)] = __dmul_rn(kp.alpha, x[u]);
+    for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, x[u]);
   } else {
     T y[M];
     apply_group<D, EP, AR, T>(kp, x, y);
 #pragma unroll
-    for (int u = 0; u < M; u++) sm[k2_slot<D, BP, EP>(u, w)] = y[u];
+    for (int u = 0; u < M; u++) sm[s[u]] = y[u];
   }
 }
 
@@ -142,11 +177,15 @@ __device__ __forceinline__ void k2_dispatch(const KParams& kp, int ep, const int
   }
 }
 
-// asynchronous global -> shared copies (cp.async, completion by commit groups)
+// asynchronous global -> shared copies (cp.async, completion by commit groups);
+// 16-byte units bypass L1
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -220,19 +259,21 @@ __device__ __forceinline__ void unrank_warp(int64_t r, int O, int (&v)[4]) {
 // id / F^d as a multiset (colex rank of the strictly increasing c_k + k), and
 // the F^d consecutive ids of the group take the fine tuples b_k = F c_k +
 // delta_k. Sorted fine tuples need delta non-decreasing where c repeats; the
-// other ids of a group are skipped. CTAs take ids id0, id0 + G, ... (G CTAs
-// in the grid), so the ids in flight at any time form a window of consecutive
-// groups: every tile row of the F^d tiles of a coarse tile (F x BL x
-// sizeof(T) contiguous bytes) is read and written at about the same time.
-// One whole warp finds the first valid id >= id0 (step G) and fills dsc.
+// other ids of a group are skipped. A CTA takes a run of consecutive ids
+// (or, persistent, every G-th id); the hardware starts CTAs in order, so the
+// ids in flight at any time form a compact window of consecutive groups:
+// every tile row of the F^d tiles of a coarse tile (F x BL x sizeof(T)
+// contiguous bytes) is read and written at about the same time, and the
+// coarse block orbits in flight lie close together in the colex order.
+// One whole warp finds the first valid id in [id, end) (step `step`) and
+// fills dsc; bp = -1 when there is none.
 template <int D>
-__device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t step, K2Desc& dsc) {
+__device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t step, int64_t end, K2Desc& dsc) {
   const int lf = kp.k2lf;
   const int nb = (kp.O + K2Shape<D>::BL - 1) / K2Shape<D>::BL;
   const int nc = ((nb - 1) >> lf) + 1;
-  const int64_t total = kp.pre[npatterns(D)];
   const int fm = (1 << lf) - 1;
-  for (; id < total; id += step) {
+  for (; id < end; id += step) {
     int v[4] = {0, 0, 0, 0};
     unrank_warp<D>(id >> (D * lf), nc + D - 1, v);
     const unsigned dl = (unsigned)id & ((1u << (D * lf)) - 1u);
@@ -280,26 +321,26 @@ __device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t s
   if ((threadIdx.x & 31) == 0) dsc.bp = -1;
 }
 
-// Copy the m_b tiles of a block orbit between HBM and shared memory. Each
-// thread owns a fixed run of VEC elements along the stride-1 index at the same
-// in-tile place of every tile (its in-tile offset, shared-memory slot and
-// global offset relative to the tile origin are computed once); per tile it
-// adds the tile's origin and checks the tile's bounds only at the upper edge.
-// LOAD: copies into shared memory, asynchronous with ASYNC (the caller
-// commits and waits), else through registers with 16-byte global loads; store: shared memory -> HBM with the beta term, 16-byte global accesses
-// where the layout allows them.
-template <int D, int VEC, bool LOAD, bool ASYNC, int MBC, typename T>
+// Copy the m_b tiles of a block orbit between HBM and shared memory in units
+// of U elements along the stride-1 index (U = 2: 16 bytes for FP64, 8 for
+// FP32; U = 1 where the tensor's strides or base addresses do not allow
+// pairs). Each thread owns fixed units at the same in-tile place of every
+// tile (global offset from the tile origin and shared-memory place computed
+// once); per tile it adds the tile's origin and checks the tile's bounds only
+// at the upper edge. LOAD: asynchronous copies into shared memory (the caller
+// commits and waits); store: shared memory -> HBM with the beta term.
+template <int D, int U, bool LOAD, typename T>
 __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& dsc) {
   using K = K2Shape<D>;
-  constexpr int CPR = K::BL / VEC;          // vector chunks per tile row
-  constexpr int CPT = K::NT / VEC;          // chunks per tile
-  // either several tiles per pass of 256 threads, or several chunks of one tile per thread
+  constexpr int CPR = K::BL / U;   // units per tile row
+  constexpr int CPT = K::NT / U;   // units per tile
+  // either several tiles per pass of 256 threads, or several units of one tile per thread
   constexpr int TPP = CPT <= 256 ? 256 / CPT : 1;
   constexpr int NCH = CPT <= 256 ? 1 : CPT / 256;
-  static_assert(CPT <= 256 ? 256 % CPT == 0 : CPT % 256 == 0, "tile chunks must tile the block");
+  static_assert(CPT <= 256 ? 256 % CPT == 0 : CPT % 256 == 0, "tile units must tile the block");
   const int64_t* ld = LOAD ? kp.lda : kp.ldb;
   const int64_t* base = dsc.base[LOAD ? 0 : 1];
-  const int mb = MBC > 0 ? MBC : dsc.mb;
+  const int mb = dsc.mb;
   const int u0 = CPT <= 256 ? threadIdx.x / CPT : 0;
   int w[NCH][4];
   int64_t goff[NCH];
@@ -307,7 +348,7 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
 #pragma unroll
   for (int q = 0; q < NCH; q++) {
     const int c = (CPT <= 256 ? threadIdx.x % CPT : threadIdx.x) + q * 256;
-    w[q][0] = (c % CPR) * VEC;
+    w[q][0] = (c % CPR) * U;
     int r = c / CPR;
 #pragma unroll
     for (int k = 1; k < 4; k++) {
@@ -318,52 +359,11 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
       }
     }
     goff[q] = 0;
-    slot[q] = 0;
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-      goff[q] += (int64_t)w[q][k] * ld[k];
-      slot[q] += w[q][k] * K::pitch(k);
-    }
+    for (int k = 0; k < D; k++) goff[q] += (int64_t)w[q][k] * ld[k];
+    slot[q] = K::phys(w[q]);  // the swizzle keeps the pair (w0 even, w0 + 1) together
   }
   T* G = LOAD ? const_cast<T*>(static_cast<const T*>(kp.A)) : static_cast<T*>(kp.B);
-  if constexpr (LOAD && !ASYNC && MBC > 0) {
-    // every load of the thread first (all in flight together), then the
-    // shared-memory writes
-    constexpr int NIT = (MBC + TPP - 1) / TPP;
-    T v[NIT][NCH][VEC];
-    unsigned inb = 0;
-#pragma unroll
-    for (int it = 0; it < NIT; it++) {
-      const int u = u0 + it * TPP;
-      if (NIT * TPP != MBC && u >= MBC) continue;
-      const bool full_u = dsc.full[u];
-#pragma unroll
-      for (int q = 0; q < NCH; q++) {
-        bool in = full_u;
-        if (!in) {
-          in = true;
-#pragma unroll
-          for (int k = 0; k < D; k++) in = in && w[q][k] < dsc.lim[u][k];
-        }
-        if (in) {
-          inb |= 1u << (it * NCH + q);
-          vload<T, VEC>(G + base[u] + goff[q], v[it][q]);
-        }
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < NIT; it++) {
-      const int u = u0 + it * TPP;
-#pragma unroll
-      for (int q = 0; q < NCH; q++) {
-        if (!(inb >> (it * NCH + q) & 1u)) continue;
-        T* sp = sm + u * K::TS + slot[q];
-#pragma unroll
-        for (int i = 0; i < VEC; i++) sp[i] = v[it][q][i];
-      }
-    }
-    return;
-  }
   const bool beta = !LOAD && (kp.flags & KF_BETA);
   const T bt = beta_of<T>(kp);
   for (int u = u0; u < mb; u += TPP) {
@@ -378,27 +378,23 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
       }
       if (!in) continue;
       T* g = G + base[u] + goff[q];
-      T* sp = sm + u * K::TS + slot[q];
-      if constexpr (LOAD && ASYNC) {
-        // the padded slots are not 16-byte aligned: element-sized copies
-#pragma unroll
-        for (int i = 0; i < VEC; i++) cp_async<sizeof(T)>(sp + i, g + i);
-      } else if constexpr (LOAD) {
-        T v[VEC];
-        vload<T, VEC>(g, v);
-#pragma unroll
-        for (int i = 0; i < VEC; i++) sp[i] = v[i];
+      T* sp = sm + u * K::NT + slot[q];
+      if constexpr (LOAD) {
+        cp_async<U * sizeof(T)>(sp, g);
       } else {
-        T v[VEC];
-#pragma unroll
-        for (int i = 0; i < VEC; i++) v[i] = sp[i];
-        if (beta) {
-          T o[VEC];
-          vload<T, VEC>(g, o);
-#pragma unroll
-          for (int i = 0; i < VEC; i++) v[i] = add_beta(v[i], o[i], bt);
+        T v[U];
+        if constexpr (U == 2) {
+          vload<T, 2>(sp, v);
+        } else {
+          v[0] = sp[0];
         }
-        vstore<T, VEC>(g, v);
+        if (beta) {
+          T o[U];
+          vload<T, U>(g, o);
+#pragma unroll
+          for (int i = 0; i < U; i++) v[i] = add_beta(v[i], o[i], bt);
+        }
+        vstore<T, U>(g, v);
       }
     }
   }
@@ -413,13 +409,8 @@ __device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, 
 #pragma unroll
   for (int k = 0; k < D; k++) T0[k] = dsc.val[Pat<D, BP>::lab(0, k)];
   for (int e0 = threadIdx.x; e0 < K::NT; e0 += blockDim.x) {
-    int w[4] = {0, 0, 0, 0};
-    int e = e0;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-      w[k] = e % K::BL;
-      e /= K::BL;
-    }
+    int w[4];
+    K::elem(e0, w);
     bool ok = T0[D - 1] * K::BL + w[D - 1] < kp.O;  // the largest coordinate of the sorted tuple
     unsigned eq = 0;
 #pragma unroll
@@ -453,104 +444,73 @@ __device__ __forceinline__ void k2_compute(const KParams& kp, const K2Desc& dsc,
   }
 }
 
-// One block orbit per CTA (SS_K2_MODE 0): the tile table is filled by warp 0,
-// the phases run with the member count m_b a compile-time constant.
-template <int D, int BP, int AR, int VEC, typename T>
-__device__ __forceinline__ void k2_one(const KParams& kp, const K2Desc& dsc, T* sm) {
-  constexpr int MB = Pat<D, BP>::M;
-  k2_copy<D, VEC, true, false, MB, T>(kp, sm, dsc);
-  __syncthreads();
-  k2_orbits<D, BP, AR, T>(kp, dsc, sm);
-  __syncthreads();
-  k2_copy<D, VEC, false, false, MB, T>(kp, sm, dsc);
-}
-
-template <int D, int AR, int VEC, typename T>
-__global__ void __launch_bounds__(256, D == 4 ? SS_K2_MINB4 : SS_K2_MINB3) k2_kernel1(const __grid_constant__ KParams kp) {
-  extern __shared__ __align__(16) unsigned char k2_smem[];
-  T* const sm = reinterpret_cast<T*>(k2_smem);
-  __shared__ K2Desc dsc;
-  if (threadIdx.x < 32) k2_next<D>(kp, blockIdx.x, kp.pre[npatterns(D)], dsc);  // this id only
-  __syncthreads();
-  switch (dsc.bp) {
-    case 0: k2_one<D, 0, AR, VEC, T>(kp, dsc, sm); break;
-    case 1: k2_one<D, 1, AR, VEC, T>(kp, dsc, sm); break;
-    case 2: k2_one<D, 2, AR, VEC, T>(kp, dsc, sm); break;
-    case 3: k2_one<D, 3, AR, VEC, T>(kp, dsc, sm); break;
-    default:
-      if constexpr (D == 4) {
-        switch (dsc.bp) {
-          case 4: k2_one<D, 4, AR, VEC, T>(kp, dsc, sm); break;
-          case 5: k2_one<D, 5, AR, VEC, T>(kp, dsc, sm); break;
-          case 6: k2_one<D, 6, AR, VEC, T>(kp, dsc, sm); break;
-          case 7: k2_one<D, 7, AR, VEC, T>(kp, dsc, sm); break;
-        }
-      }
-  }
-}
-
-// CTAs over the block orbits of their id list (one id each when the grid
-// covers all ids). With NBUF = 2 (persistent CTAs) the tiles of the next block
-// orbit are copied asynchronously into the second buffer while the current
-// one is computed and stored back; with NBUF = 1 the phases follow one
-// another. Block orbits own disjoint tiles, so in place the prefetch of
-// the next orbit never reads an element the current one writes. The tile
-// tables rotate through three slots: the one being filled for the next orbit
-// is neither the current one nor the one the previous orbit's stores may
-// still be reading.
-template <int D, int AR, int VEC, int NBUF, typename T>
-__global__ void __launch_bounds__(256, D == 4 ? 2 : 1) k2_kernel(const __grid_constant__ KParams kp) {
+// A CTA works through the block orbits of its ids. With NBUF = 2 the tiles of
+// the next block orbit are copied asynchronously into the second buffer
+// while the current one is computed and stored back; with NBUF = 1 the
+// phases follow one another. Block orbits own disjoint tiles, so in place the
+// prefetch of the next orbit never reads an element the current one writes.
+// The tile tables rotate through three slots: the one being filled for the
+// next orbit is neither the current one nor the one the previous orbit's
+// stores may still be reading.
+template <int D, int AR, int U, int NBUF, int RUN, int MINB, typename T>
+__global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ KParams kp) {
   using K = K2Shape<D>;
   extern __shared__ __align__(16) unsigned char k2_smem[];
   T* const buf0 = reinterpret_cast<T*>(k2_smem);
-  T* const buf1 = buf0 + (NBUF > 1 ? fact(D) * K::TS : 0);
+  T* const buf1 = buf0 + (NBUF > 1 ? fact(D) * K::NT : 0);
   __shared__ K2Desc dsc[3];
   const bool w0 = threadIdx.x < 32;
-  if (w0) k2_next<D>(kp, blockIdx.x, gridDim.x, dsc[0]);
+  // ids of this CTA: a run of RUN consecutive ids, or (RUN = 0) every
+  // gridDim.x-th id from blockIdx.x
+  const int64_t total = kp.pre[npatterns(D)];
+  const int64_t first = RUN > 0 ? (int64_t)blockIdx.x * RUN : (int64_t)blockIdx.x;
+  const int64_t step = RUN > 0 ? 1 : (int64_t)gridDim.x;
+  const int64_t end = RUN > 0 ? (first + RUN < total ? first + RUN : total) : total;
+  if (w0) k2_next<D>(kp, first, step, end, dsc[0]);
   __syncthreads();
   if (dsc[0].bp < 0) return;
   if constexpr (NBUF > 1) {
-    k2_copy<D, VEC, true, true, 0, T>(kp, buf0, dsc[0]);
+    k2_copy<D, U, true, T>(kp, buf0, dsc[0]);
     cp_async_commit();
   }
   for (int k = 0;; k++) {
     const K2Desc& cur = dsc[k % 3];
     K2Desc& nxt = dsc[(k + 1) % 3];
-    T* const cb = (k & 1) ? buf1 : buf0;
+    T* const cb = NBUF > 1 && (k & 1) ? buf1 : buf0;
     if constexpr (NBUF > 1) {
-      if (w0) k2_next<D>(kp, cur.id + gridDim.x, gridDim.x, nxt);
+      if (w0) k2_next<D>(kp, cur.id + step, step, end, nxt);
       __syncthreads();  // nxt ready; the previous orbit's stores from the other buffer are done
-      if (nxt.bp >= 0) k2_copy<D, VEC, true, true, 0, T>(kp, (k & 1) ? buf0 : buf1, nxt);
+      if (nxt.bp >= 0) k2_copy<D, U, true, T>(kp, (k & 1) ? buf0 : buf1, nxt);
       cp_async_commit();
       cp_async_wait<1>();  // this thread's copies of the current orbit have landed
     } else {
-      k2_copy<D, VEC, true, false, 0, T>(kp, cb, cur);
+      k2_copy<D, U, true, T>(kp, cb, cur);
+      cp_async_commit();
+      cp_async_wait<0>();
     }
     __syncthreads();
     k2_compute<D, AR, T>(kp, cur, cb);
     __syncthreads();
-    k2_copy<D, VEC, false, false, 0, T>(kp, cb, cur);
+    k2_copy<D, U, false, T>(kp, cb, cur);
     if constexpr (NBUF == 1) {
-      if (w0) k2_next<D>(kp, cur.id + gridDim.x, gridDim.x, nxt);
+      if (w0) k2_next<D>(kp, cur.id + step, step, end, nxt);
       __syncthreads();  // nxt ready; the buffer is free again
     }
     if (nxt.bp < 0) break;
   }
 }
 
-// Launch shapes (SS_K2_MODE): 0 = one CTA per id (k2_kernel1); 2 =
-// persistent CTAs with two buffers (k2_kernel), where two buffers leave room
-// for more than one CTA per SM.
-template <int D, typename T>
-constexpr int k2_nbuf() {
-  return SS_K2_MODE == 2 && 2 * (size_t)fact(D) * K2Shape<D>::TS * sizeof(T) <= 100 * 1024 ? 2 : 1;
-}
-
-template <int D, int AR, int VEC, typename T>
+// Launch shape: SS_K2_NBUF3 / SS_K2_NBUF4 buffers of d! dense tiles per CTA,
+// SS_K2_RUN3 / SS_K2_RUN4 consecutive ids per CTA (0: a persistent grid of
+// the resident CTAs) and SS_K2_MINB3 / SS_K2_MINB4 resident CTAs per SM for
+// the register budget.
+template <int D, int AR, int U, typename T>
 cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
-  constexpr int NBUF = k2_nbuf<D, T>();
-  constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::TS * sizeof(T);
-  auto fn = NBUF == 2 ? k2_kernel<D, AR, VEC, 2, T> : k2_kernel1<D, AR, VEC, T>;
+  constexpr int NBUF = D == 3 ? SS_K2_NBUF3 : SS_K2_NBUF4;
+  constexpr int MINB = D == 3 ? SS_K2_MINB3 : SS_K2_MINB4;
+  constexpr int RUN = D == 3 ? SS_K2_RUN3 : SS_K2_RUN4;
+  constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
+  auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
   constexpr int MAXDEV = 64;
   static int ctas[MAXDEV] = {0};  // resident CTAs per device (persistent grid)
   int dev = 0;
@@ -573,18 +533,18 @@ cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
   }
   const int64_t ids = kp.pre[npatterns(D)];
   if (ids == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(NBUF == 2 && ids > ctas[dev] ? ctas[dev] : ids);
+  const unsigned grid = (unsigned)(RUN > 0 ? (ids + RUN - 1) / RUN : (ids > ctas[dev] ? ctas[dev] : ids));
   fn<<<grid, 256, smem, st>>>(kp);
   return cudaGetLastError();
 }
 
-// 16-byte runs along the stride-1 index when the tensor allows them
+// element pairs along the stride-1 index when the tensor allows them
 template <int D, int AR, typename T>
 cudaError_t launch_k2_impl(const KParams& kp, cudaStream_t st) {
-  constexpr int V = 16 / sizeof(T);
-  bool vec = (kp.O % V == 0) && ((uintptr_t)kp.A % 16 == 0) && ((uintptr_t)kp.B % 16 == 0);
-  for (int k = 1; k < D; k++) vec = vec && (kp.lda[k] % V == 0) && (kp.ldb[k] % V == 0);
-  if (vec) return launch_k2_vec<D, AR, V, T>(kp, st);
+  constexpr uintptr_t PB = 2 * sizeof(T);
+  bool pair = (kp.O % 2 == 0) && ((uintptr_t)kp.A % PB == 0) && ((uintptr_t)kp.B % PB == 0);
+  for (int k = 1; k < D; k++) pair = pair && (kp.lda[k] % 2 == 0) && (kp.ldb[k] % 2 == 0);
+  if (pair) return launch_k2_vec<D, AR, 2, T>(kp, st);
   return launch_k2_vec<D, AR, 1, T>(kp, st);
 }
 
