@@ -149,10 +149,20 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
+# the sources that define each profiled kernel's code and launch (a committed
+# DRAM-traffic figure is used only while these are unchanged)
+KERNEL_SOURCES = {
+    "k1": ("ss_internal.h", "ss_kernels.cuh", "ss_k1_d3.cu", "ss_k1_d4_exact.cu", "ss_host.cpp", "ss_status.cu"),
+    "k2": ("ss_internal.h", "ss_kernels.cuh", "ss_k2.cuh", "ss_k2_d3.cu", "ss_k2_d4_exact.cu", "ss_host.cpp",
+           "ss_status.cu"),
+}
+CASE_KERNEL = {"3d": "k1", "3d-small": "k1", "4d": "k1", "4d-small": "k1", "paper-3d": "k2", "paper-4d": "k2"}
+
+
+def kernel_source_hash(kernel: str = "k1") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1705_06661_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(f.encode())
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
@@ -160,15 +170,15 @@ def kernel_source_hash() -> str:
 
 def ncu_traffic(case: str):
     """DRAM bytes per launch from the committed ncu summary, only if the
-    kernel sources are unchanged since it was taken."""
+    kernel's sources are unchanged since it was taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except (OSError, ValueError):
         return None
-    if rec.get("source_hash") != kernel_source_hash():
-        return None
     c = rec.get("cases", {}).get(case)
-    return None if c is None else c.get("dram_bytes_per_launch")
+    if c is None or c.get("source_hash") != kernel_source_hash(CASE_KERNEL[case]):
+        return None
+    return c.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(seconds: float = 10.0):
