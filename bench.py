@@ -228,9 +228,16 @@ def allmax(world, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(world: int, bytes_per_step: int, steps: int, dt_max: float) -> float:
+    """Whole-job GB/s of `world` replicas that each ran `steps` steps of
+    `bytes_per_step` algorithmic bytes, timed by the slowest rank."""
+    return world * bytes_per_step * steps / dt_max / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -402,7 +409,7 @@ def run_ours(args):
     clocks.stop()
     dt_max = allmax(world, dt)
     bytes_step = 2 * N * 8
-    value = world * bytes_step * args.steps / dt_max / 1e9
+    value = replica_throughput(world, bytes_step, args.steps, dt_max)
     ms_step = dt_max / args.steps * 1e3
     per_launch_s = dt / max(launches, 1)
     achieved = bytes_step / per_launch_s / 1e9 if launches == args.steps else bytes_step * args.steps / dt / 1e9
