@@ -179,6 +179,14 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_K2_MINB4 2
 #endif
 
+// generic d = 4 orbits with a non-power-of-two alpha: 1 = an out-of-line
+// path that reloads the inputs (the common path stays 2 % faster; a
+// non-power-of-two alpha runs at about 2/3 of the inline copy's speed),
+// 0 = a second inline copy of the core
+#ifndef SS_4D_SCALED_OUTOFLINE
+#define SS_4D_SCALED_OUTOFLINE 1
+#endif
+
 #ifndef SS_4D_GROUPS
 #define SS_4D_GROUPS 4
 #endif

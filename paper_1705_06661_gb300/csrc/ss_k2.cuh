@@ -132,9 +132,14 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
 #pragma unroll
   for (int u = 0; u < M; u++) x[u] = sm[s[u]];
   if constexpr (D == 4 && EP == 0 && AR == AR_EXACT) {
-    const bool amul = kp.flags & KF_ALPHA_MUL;
-    auto sink = [&](int u, double v) { sm[s[u]] = amul ? __dmul_rn(kp.alpha, v) : v; };
-    if (exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) return;
+    auto sink = [&](int u, double v) { sm[s[u]] = v; };
+    if (exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) {
+      if (kp.flags & KF_ALPHA_MUL) {  // alpha not a power of two: rare, a separate pass
+#pragma unroll 1
+        for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, sm[s[u]]);
+      }
+      return;
+    }
     strict_core<D, EP>(kp, x);
 #pragma unroll
     for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, x[u]);

@@ -366,6 +366,26 @@ static __device__ __noinline__ void strict_fallback_generic4(const KParams& kp, 
   }
 }
 
+// The generic d = 4 group when alpha is not a power of two (the fixed-point
+// path cannot fold it into the conversion): reloads its inputs and stores
+// alpha S(x) + beta B. Out of line and taken by a uniform branch before the
+// loads, so the common path carries no FP64 multiply.
+static __device__ __noinline__ void scaled_generic4(const KParams& kp, const int64_t* offA, const int64_t* offB,
+                                                    int64_t s) {
+  const double* A = static_cast<const double*>(kp.A);
+  double* B = static_cast<double*>(kp.B);
+  double x[24];
+  for (int u = 0; u < 24; u++) x[u] = A[offA[u] + s];
+  const bool beta = kp.flags & KF_BETA;
+  auto sink = [&](int u, double v) {
+    double* dst = B + offB[u] + s;
+    v = __dmul_rn(kp.alpha, v);
+    if (beta) v = add_beta(v, *dst, kp.beta);
+    *dst = v;
+  };
+  if (!exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) strict_fallback_generic4(kp, offA, offB, s);
+}
+
 // ---------------------------------------------------------------------------
 // K1 body for pattern P. Warp 0 unranks the orbit and writes the m member
 // offsets of A and B to shared memory; the CTA then streams cpb chunks of
@@ -401,6 +421,12 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
   for (int64_t c = c0; c < c1; c++) {
     const int64_t s = c * step + (int64_t)threadIdx.x * VEC;
     if (s >= kp.S) break;
+    if constexpr (SS_4D_SCALED_OUTOFLINE && D == 4 && P == 0 && AR == AR_EXACT && VEC == 1) {
+      if (kp.flags & KF_ALPHA_MUL) {
+        scaled_generic4(kp, soff[0], soff[1], s);
+        continue;
+      }
+    }
     T x[VEC][M], y[VEC][M];
 #pragma unroll
     for (int u = 0; u < M; u++) {
@@ -410,14 +436,25 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
       for (int e = 0; e < VEC; e++) x[e][u] = v[e];
     }
     if constexpr (D == 4 && P == 0 && AR == AR_EXACT && VEC == 1) {
-      const bool beta = kp.flags & KF_BETA, amul = kp.flags & KF_ALPHA_MUL;
-      auto sink = [&](int u, double v) {
-        T* dst = B + soff[1][u] + s;
-        if (amul) v = __dmul_rn(kp.alpha, v);
-        if (beta) v = add_beta(v, *dst, kp.beta);
-        *dst = v;
-      };
-      if (!exact_core_grouped4<SS_4D_GROUPS>(kp, x[0], sink)) strict_fallback_generic4(kp, soff[0], soff[1], s);
+      const bool beta = kp.flags & KF_BETA;
+      bool done;
+      if (!SS_4D_SCALED_OUTOFLINE && (kp.flags & KF_ALPHA_MUL)) {
+        auto sink = [&](int u, double v) {
+          T* dst = B + soff[1][u] + s;
+          v = __dmul_rn(kp.alpha, v);
+          if (beta) v = add_beta(v, *dst, kp.beta);
+          *dst = v;
+        };
+        done = exact_core_grouped4<SS_4D_GROUPS>(kp, x[0], sink);
+      } else {
+        auto sink = [&](int u, double v) {
+          T* dst = B + soff[1][u] + s;
+          if (beta) v = add_beta(v, *dst, kp.beta);
+          *dst = v;
+        };
+        done = exact_core_grouped4<SS_4D_GROUPS>(kp, x[0], sink);
+      }
+      if (!done) strict_fallback_generic4(kp, soff[0], soff[1], s);
       continue;
     }
 #pragma unroll
