@@ -187,6 +187,11 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_4D_SCALED_OUTOFLINE 1
 #endif
 
+// batched kernel (3D): resident CTAs per SM the register budget is sized for
+#ifndef SS_KB_MINB3
+#define SS_KB_MINB3 4
+#endif
+
 #ifndef SS_4D_GROUPS
 #define SS_4D_GROUPS 4
 #endif

@@ -540,7 +540,7 @@ __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int6
 }
 
 template <int D, int AR, typename T>
-__global__ void __launch_bounds__(256) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
+__global__ void __launch_bounds__(256, D == 3 ? SS_KB_MINB3 : 1) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
                                                  const int* __restrict__ vecs, int n) {
   __shared__ KParams skp;
   const int64_t total = prefix[n];
