@@ -152,10 +152,31 @@ int64_t binom(int n, int k) {
   return r;
 }
 
+// the pattern tables and matrix offsets, built once per process (building
+// them per call cost about 0.5 ms of host time for d = 4)
 template <int D>
-int pattern_nd(int P) { return make_pattern<D>(P).nd; }
+const Pattern<D>& host_pattern(int P) {
+  static const std::array<Pattern<D>, 8> t = [] {
+    std::array<Pattern<D>, 8> a{};
+    for (int p = 0; p < npatterns(D); p++) a[p] = make_pattern<D>(p);
+    return a;
+  }();
+  return t[P];
+}
 template <int D>
-int pattern_m(int P) { return make_pattern<D>(P).m; }
+int host_mp_offset(int P) {
+  static const std::array<int, 9> t = [] {
+    std::array<int, 9> a{};
+    for (int p = 0; p < npatterns(D); p++) a[p] = mp_offset<D>(p);
+    return a;
+  }();
+  return t[P];
+}
+
+template <int D>
+int pattern_nd(int P) { return host_pattern<D>(P).nd; }
+template <int D>
+int pattern_m(int P) { return host_pattern<D>(P).m; }
 
 int nd_of(int d, int P) { return d == 3 ? pattern_nd<3>(P) : pattern_nd<4>(P); }
 
@@ -163,8 +184,8 @@ int nd_of(int d, int P) { return d == 3 ? pattern_nd<3>(P) : pattern_nd<4>(P); }
 template <int D>
 void fill_mp(const std::vector<long long>& a, int* mp) {
   for (int P = 1; P < npatterns(D); P++) {
-    const Pattern<D> pt = make_pattern<D>(P);
-    int* M = mp + mp_offset<D>(P);
+    const Pattern<D>& pt = host_pattern<D>(P);
+    int* M = mp + host_mp_offset<D>(P);
     for (int u = 0; u < pt.m; u++)
       for (int v = 0; v < pt.m; v++) M[u * pt.m + v] = 0;
     for (int u = 0; u < pt.m; u++)
