@@ -442,7 +442,11 @@ int plan_one(const Request& r, Launch* L) {
     } else {
       const int64_t per = 256LL * vec;
       kp.nchunk = (S + per - 1) / per;
-      kp.cpb = (int)std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+      // about 8192 positions per member per block, spread evenly over the
+      // blocks of an orbit (40 chunks: 20 + 20, not 32 + 8)
+      const int64_t cpb0 = std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+      const int64_t nbo = (kp.nchunk + cpb0 - 1) / cpb0;
+      kp.cpb = (int)((kp.nchunk + nbo - 1) / nbo);
       const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
       kp.pre[0] = 0;
       for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
