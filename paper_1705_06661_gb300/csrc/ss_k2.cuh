@@ -413,20 +413,29 @@ __device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, 
   int T0[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < D; k++) T0[k] = dsc.val[Pat<D, BP>::lab(0, k)];
-  for (int e0 = threadIdx.x; e0 < K::NT; e0 += blockDim.x) {
+  // the equal block coordinates are those with equal labels in the block
+  // pattern (compile time): for distinct blocks every offset is canonical and
+  // the element pattern is the generic one
+  const bool edge = T0[D - 1] * K::BL + K::BL > kp.O;  // the largest coordinate's tile is cut by the edge
+#pragma unroll 1
+  for (int e0 = threadIdx.x; e0 < K::NT; e0 += 256) {
     int w[4];
     K::elem(e0, w);
-    bool ok = T0[D - 1] * K::BL + w[D - 1] < kp.O;  // the largest coordinate of the sorted tuple
+    bool ok = !edge || T0[D - 1] * K::BL + w[D - 1] < kp.O;
     unsigned eq = 0;
 #pragma unroll
     for (int k = 0; k + 1 < D; k++) {
-      if (T0[k] == T0[k + 1]) {
+      if (Pat<D, BP>::lab(0, k) == Pat<D, BP>::lab(0, k + 1)) {
         ok = ok && w[k] <= w[k + 1];  // canonical: sorted within equal blocks
         if (w[k] == w[k + 1]) eq |= 1u << k;
       }
     }
     if (!ok) continue;
-    k2_dispatch<D, BP, AR, T>(kp, k2_elem_pattern<D>(eq), w, sm);
+    if constexpr (BP == 0) {
+      if constexpr (kK2Map<D, BP, 0>.valid) k2_group<D, BP, 0, AR, T>(kp, w, sm);
+    } else {
+      k2_dispatch<D, BP, AR, T>(kp, k2_elem_pattern<D>(eq), w, sm);
+    }
   }
 }
 
