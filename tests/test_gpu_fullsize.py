@@ -10,6 +10,8 @@ OpenMP over the host cores).
   and FP32 storage; per-block errors against the FP64 oracle.
 - 4D, A[10]^8 through autograd: forward and backward against the oracle and
   its literal transpose.
+- The paper's layout (tiled kernel): 3D A[544]^3 and 4D A[112]^4, out of place
+  and, integer-valued, in place.
 """
 import numpy as np
 import pytest
@@ -115,3 +117,25 @@ def test_config5_autograd_full():
                   "config 5 forward")
     assert_within(A.grad.cpu().numpy(), oracle.spinsum_transpose(G_np, 4, coef), fp64_tol(4, coef, False, G_np),
                   "config 5 backward")
+
+
+@pytest.mark.parametrize("d,N,row", [(3, 544, 1), (4, 112, 5)])
+def test_paper_layout_full(d, N, row):
+    """The paper-layout benchmark tensors (tiled kernel): 3D A[544]^3 and 4D
+    A[112]^4, Table II row 1 / row 5 factorized out of place against the
+    oracle over the whole output; an integer-valued copy in place, bit-exact."""
+    import oracle
+    import paper_1705_06661_gb300 as ss
+    shape = (N,) * d
+    coef = wl.table2(row)
+    A_np = wl.uniform(3, shape)
+    want = oracle.spinsum(A_np, d, coef, factorized=True)
+    A = _dev(A_np)
+    B = ss.colmajor_like(A)
+    ss.spinsum(A, coef, d=d, out=B, factorized=True)
+    assert_within(_host(B), want, fp64_tol(d, coef, True, A_np), f"paper layout {d}d N={N}")
+    del A, B, want
+    Ai_np = wl.integers(3, shape)
+    Ai = _dev(Ai_np)
+    ss.spinsum(Ai, coef, d=d, inplace=True, factorized=True)
+    assert_bitexact(_host(Ai), oracle.spinsum(Ai_np, d, coef, factorized=True), f"paper layout {d}d N={N} integer")
