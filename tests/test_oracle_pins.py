@@ -391,3 +391,27 @@ def test_transpose_of_factor_chain_reverses_order(oracle_mod):
     st = oracle_mod.spinsum_transpose(y, d, np.stack([F1, F2]))
     want = oracle_mod.spinsum(oracle_mod.spinsum(y, d, _inverse_coefs(d, F1)), d, _inverse_coefs(d, F2))
     np.testing.assert_array_equal(st, want)
+
+
+def test_table2_flop_reduction_factors(oracle_mod):
+    """Sec. 5: factorization reduces the FLOP count of test cases 1, 2-4, 5,
+    6-17 and 18-21 by 2x, 1x, 4x, 2x and 1x, and cases 6-17 all need the same
+    number of operations. Counting the additions per output element (terms - 1
+    expanded against the sum of terms - 1 over the factors) and rounding gives
+    these factors exactly under the repaired reading of Table II, including the
+    garbled rows 8-11, 16 and 17; a wrong sign or a missing term in any factor
+    changes a count."""
+    want = {1: 2, 5: 4}
+    want.update({r: 1 for r in (2, 3, 4, 18, 19, 20, 21)})
+    want.update({r: 2 for r in range(6, 18)})
+    counts = {}
+    for row in wl.TABLE2_ROWS:
+        d = wl.table2_dim(row)
+        chain = np.atleast_2d(wl.table2(row))
+        expanded = oracle_mod.expand(d, chain)
+        adds_exp = int(np.count_nonzero(expanded)) - 1
+        adds_fac = int(sum(np.count_nonzero(f) - 1 for f in chain))
+        assert round(adds_exp / adds_fac) == want[row], (row, adds_exp, adds_fac)
+        counts[row] = (adds_exp, adds_fac)
+    assert len({counts[r] for r in range(6, 18)}) == 1
+    assert max(counts, key=lambda r: counts[r][0] / counts[r][1]) == 5
