@@ -193,7 +193,7 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #endif
 
 #ifndef SS_4D_GROUPS
-#define SS_4D_GROUPS 4
+#define SS_4D_GROUPS 3
 #endif
 #ifndef SS_4D_MINBLOCKS
 #define SS_4D_MINBLOCKS 3
