@@ -102,6 +102,14 @@ int spinsum_3d(int dtype, const int64_t ext[6], const void* A, const int64_t lda
                const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
                int inplace, spinsum_stream_t stream);
 
+/* spinsum_2d -- 2D spin summation on a 4-index tensor (Def. 3 with d = 2, the
+ * CCSD case of Sec. 1): ext[0..1] spectators a,b; ext[2..3] permuted i,j
+ * (equal); coef is nfactors x 2 doubles (identity, then the transposition).
+ * Otherwise as spinsum_3d. */
+int spinsum_2d(int dtype, const int64_t ext[4], const void* A, const int64_t lda[4], void* B,
+               const int64_t ldb[4], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream);
+
 /* spinsum_4d -- 4D spin summation on an 8-index tensor (Def. 3 with d = 4):
  * ext[0..3] spectators a,b,c,d; ext[4..7] permuted i,j,k,l (all equal);
  * coef is nfactors x 24 doubles. Otherwise as spinsum_3d. */
@@ -133,6 +141,9 @@ int spinsum_4d(int dtype, const int64_t ext[8], const void* A, const int64_t lda
 int spinsum_3d_host(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
                     const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
                     int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
+int spinsum_2d_host(int dtype, const int64_t ext[4], const void* A, const int64_t lda[4], void* B,
+                    const int64_t ldb[4], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
 int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_t lda[8], void* B,
                     const int64_t ldb[8], const double* coef, int nfactors, int mode, double alpha, double beta,
                     int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
@@ -142,7 +153,8 @@ int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_
  * mixed coefficient sets) run by one persistent kernel launch.
  *
  * spinsum_problem describes one summation exactly as the arguments of
- * spinsum_3d / spinsum_4d do (d = 3 uses the first 6 entries of ext/lda/ldb).
+ * spinsum_2d / spinsum_3d / spinsum_4d do (d = 2 uses the first 4 entries of
+ * ext/lda/ldb, d = 3 the first 6).
  * spinsum_plan_create validates every problem, builds the device work list
  * (the plan allocates and owns that device memory until destroyed), copies the
  * coefficients, and picks tile sizes with its autotuner (which times
@@ -153,7 +165,7 @@ int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_
  * it allocates nothing and may be captured in a CUDA graph.
  */
 typedef struct spinsum_problem {
-  int d;            /* 3 or 4 */
+  int d;            /* 2, 3 or 4 */
   int64_t ext[8];   /* d spectators then d permuted extents */
   const void* A;
   int64_t lda[8];

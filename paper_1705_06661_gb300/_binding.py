@@ -72,12 +72,12 @@ def _load() -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     sig = [ctypes.c_int, _I64P, _VP, _I64P, _VP, _I64P, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
            ctypes.c_double, ctypes.c_int, _VP]
-    for name in ("spinsum_3d", "spinsum_4d"):
+    for name in ("spinsum_2d", "spinsum_3d", "spinsum_4d"):
         f = getattr(lib, name)
         f.argtypes = sig
         f.restype = ctypes.c_int
     hsig = sig[:-1] + [_VP, ctypes.c_size_t, _VP]
-    for name in ("spinsum_3d_host", "spinsum_4d_host"):
+    for name in ("spinsum_2d_host", "spinsum_3d_host", "spinsum_4d_host"):
         f = getattr(lib, name)
         f.argtypes = hsig
         f.restype = ctypes.c_int
@@ -134,6 +134,11 @@ def _call(fn, n, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, 
                      int(nfactors), int(mode), float(alpha), float(beta), int(inplace), _VP(stream)))
 
 
+def spinsum_2d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream) -> int:
+    """spinsum_2d of the C-ABI; A, B and stream are integer addresses."""
+    return _call(lib.spinsum_2d, 4, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream)
+
+
 def spinsum_3d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream) -> int:
     """spinsum_3d of the C-ABI; A, B and stream are integer addresses."""
     return _call(lib.spinsum_3d, 6, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream)
@@ -152,6 +157,13 @@ def _call_host(fn, n, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, b
     return _check(fn(int(dtype), _i64(ext), _VP(A), _i64(lda), _VP(B), _i64(ldb), _VP(c.ctypes.data),
                      int(nfactors), int(mode), float(alpha), float(beta), int(inplace), _VP(ws),
                      ctypes.c_size_t(int(ws_bytes)), _VP(stream)))
+
+
+def spinsum_2d_host(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, workspace,
+                    workspace_bytes, stream) -> int:
+    """spinsum_2d_host of the C-ABI; A and B are host addresses, workspace a device address."""
+    return _call_host(lib.spinsum_2d_host, 4, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta,
+                      inplace, workspace, workspace_bytes, stream)
 
 
 def spinsum_3d_host(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, workspace,

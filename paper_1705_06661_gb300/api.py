@@ -60,8 +60,8 @@ def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | 
     coefficient chain `coef` ([nfactors, d!], lexicographic permutation order)."""
     if d is None:
         d = A.dim() // 2
-    if d not in (3, 4):
-        raise ValueError("d must be 3 or 4")
+    if d not in (2, 3, 4):
+        raise ValueError("d must be 2, 3 or 4")
     if not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
     if A.dtype == torch.float64:
@@ -84,7 +84,7 @@ def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | 
     mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
         | (_b.SPINSUM_STRICT if strict else 0) | (_b.SPINSUM_TMA if tma else 0)
     st = (stream or torch.cuda.current_stream(A.device)).cuda_stream
-    fn = _b.spinsum_3d if d == 3 else _b.spinsum_4d
+    fn = {2: _b.spinsum_2d, 3: _b.spinsum_3d, 4: _b.spinsum_4d}[d]
     with torch.cuda.device(A.device):
         fn(dtype, ext, A.data_ptr(), lda, out.data_ptr(), ldb, c, c.shape[0], mode, alpha, beta, int(inplace), st)
     return out
@@ -122,7 +122,7 @@ def spinsum_host(A: torch.Tensor, coef, *, out: torch.Tensor | None = None, work
     mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
         | (_b.SPINSUM_STRICT if strict else 0)
     st = (stream or torch.cuda.current_stream(workspace.device)).cuda_stream
-    fn = _b.spinsum_3d_host if d == 3 else _b.spinsum_4d_host
+    fn = {2: _b.spinsum_2d_host, 3: _b.spinsum_3d_host, 4: _b.spinsum_4d_host}[d]
     with torch.cuda.device(workspace.device):
         fn(dtype, ext, A.data_ptr(), lda, out.data_ptr(), ldb, c, c.shape[0], mode, alpha, beta, int(inplace),
            workspace.data_ptr(), workspace.numel(), st)

@@ -98,8 +98,8 @@ Group make_group(int d) {
 }
 
 const Group& group(int d) {
-  static const Group g3 = make_group(3), g4 = make_group(4);
-  return d == 3 ? g3 : g4;
+  static const Group g2 = make_group(2), g3 = make_group(3), g4 = make_group(4);
+  return d == 2 ? g2 : (d == 3 ? g3 : g4);
 }
 
 // product of a chain F_1 .. F_k (B = F_1(...F_k(A))): left fold, each entry
@@ -178,7 +178,7 @@ int pattern_nd(int P) { return host_pattern<D>(P).nd; }
 template <int D>
 int pattern_m(int P) { return host_pattern<D>(P).m; }
 
-int nd_of(int d, int P) { return d == 3 ? pattern_nd<3>(P) : pattern_nd<4>(P); }
+int nd_of(int d, int P) { return d == 2 ? pattern_nd<2>(P) : (d == 3 ? pattern_nd<3>(P) : pattern_nd<4>(P)); }
 
 // dense expanded orbit matrices of the degenerate patterns
 template <int D>
@@ -228,7 +228,7 @@ void span(int n, const int64_t* ext, const int64_t* ld, const void* base, size_t
 
 int plan_one(const Request& r, Launch* L) {
   const int d = r.d;
-  if (d != 3 && d != 4) return fail(SPINSUM_ERR_ARG, "d must be 3 or 4");
+  if (d < 2 || d > 4) return fail(SPINSUM_ERR_ARG, "d must be 2, 3 or 4");
   if (r.dtype != SPINSUM_F64 && r.dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", r.dtype);
   if (r.mode & ~(SPINSUM_FACTORIZED | SPINSUM_ADJOINT | SPINSUM_STRICT | SPINSUM_TMA))
     return fail(SPINSUM_ERR_ARG, "unknown mode bits 0x%x", r.mode);
@@ -395,7 +395,8 @@ int plan_one(const Request& r, Launch* L) {
             kp.nci = 1;
             for (int s = 0; s < g.n; s++) kp.ci[0][s] = (int)ex[s];
           }
-          if (d == 3) fill_mp<3>(ex, kp.mp);
+          if (d == 2) fill_mp<2>(ex, kp.mp);
+          else if (d == 3) fill_mp<3>(ex, kp.mp);
           else fill_mp<4>(ex, kp.mp);
         }
       }
@@ -421,7 +422,7 @@ int plan_one(const Request& r, Launch* L) {
   if (dense && S >= 64) {
     L->kernel = 0;
     int vec = 1;
-    const int want = d == 3 ? (r.dtype == SPINSUM_F64 ? 2 : 4) : 1;
+    const int want = d <= 3 ? (r.dtype == SPINSUM_F64 ? 2 : 4) : 1;
     bool aligned = (S % want == 0) && ((uintptr_t)r.A % (es * want) == 0) && ((uintptr_t)r.B % (es * want) == 0);
     for (int k = 0; k < d; k++) aligned = aligned && (kp.lda[k] % want == 0) && (kp.ldb[k] % want == 0);
     if (aligned && want > 1) vec = want;
@@ -457,10 +458,10 @@ int plan_one(const Request& r, Launch* L) {
     // the paper's layout: no spectators, the first permuted index at stride 1 --
     // tiled block orbits through shared memory (K2)
     L->kernel = 3;
-    const int bl = d == 3 ? 8 : 4;
+    const int bl = d == 2 ? 32 : (d == 3 ? 8 : 4);
     const int nb = (O + bl - 1) / bl;
     // CTAs in groups of F^d over sorted coarse tuples (multisets of d of nc values)
-    kp.k2lf = d == 3 ? SS_K2_LF3 : SS_K2_LF4;
+    kp.k2lf = d == 2 ? SS_K2_LF2 : (d == 3 ? SS_K2_LF3 : SS_K2_LF4);
     const int64_t nc = ((nb - 1) >> kp.k2lf) + 1;
     const int64_t grid = binom(nc + d - 1, d) << (d * kp.k2lf);
     for (int p = 0; p <= 8; p++) kp.pre[p] = p < np ? 0 : grid;
@@ -494,6 +495,13 @@ int run(const Request& r, cudaStream_t st) {
 }  // namespace
 
 extern "C" {
+
+int spinsum_2d(int dtype, const int64_t ext[4], const void* A, const int64_t lda[4], void* B,
+               const int64_t ldb[4], const double* coef, int nfactors, int mode, double alpha, double beta,
+               int inplace, spinsum_stream_t stream) {
+  Request r{2, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run(r, (cudaStream_t)stream);
+}
 
 int spinsum_3d(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
                const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
@@ -570,7 +578,7 @@ int host_pipe(HostPipe** out) {
 int run_host(const Request& r, void* ws, size_t ws_bytes, cudaStream_t user) {
   t_err.clear();
   const int d = r.d;
-  if (d != 3 && d != 4) return fail(SPINSUM_ERR_ARG, "d must be 3 or 4");
+  if (d < 2 || d > 4) return fail(SPINSUM_ERR_ARG, "d must be 2, 3 or 4");
   if (!r.ext || !r.lda || !r.ldb) return fail(SPINSUM_ERR_ARG, "null extent or stride array");
   if (r.dtype != SPINSUM_F64 && r.dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", r.dtype);
   const size_t es = r.dtype == SPINSUM_F64 ? 8 : 4;
@@ -686,6 +694,13 @@ int run_host(const Request& r, void* ws, size_t ws_bytes, cudaStream_t user) {
 
 extern "C" {
 
+int spinsum_2d_host(int dtype, const int64_t ext[4], const void* A, const int64_t lda[4], void* B,
+                    const int64_t ldb[4], const double* coef, int nfactors, int mode, double alpha, double beta,
+                    int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream) {
+  Request r{2, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace};
+  return run_host(r, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
 int spinsum_3d_host(int dtype, const int64_t ext[6], const void* A, const int64_t lda[6], void* B,
                     const int64_t ldb[6], const double* coef, int nfactors, int mode, double alpha, double beta,
                     int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream) {
@@ -744,7 +759,7 @@ ImageShape image_shape(int n) {
   ImageShape sh;
   sh.probs = 0;
   sh.prefix = sizeof(KParams) * (size_t)n;
-  sh.vec = sh.prefix + sizeof(int64_t) * (size_t)(n + 8);
+  sh.vec = sh.prefix + sizeof(int64_t) * (size_t)(n + BATCH_MAX_CLASSES);
   sh.bytes = sh.vec + sizeof(int) * (size_t)n;
   return sh;
 }
@@ -756,7 +771,7 @@ std::vector<ClassRange> fill_batch(const std::vector<Launch>& ls, const std::vec
                                    BatchLayout out, int* status) {
   std::vector<ClassRange> cls;
   int next = 0, pnext = 0;
-  for (int d : {3, 4})
+  for (int d : {2, 3, 4})
     for (int ar : {(int)AR_EXACT, (int)AR_STRICT, (int)AR_F32}) {
       ClassRange c{d, ar, next, pnext, 0, 0};
       for (int i : order) {

@@ -147,7 +147,10 @@ constexpr int MP_MAX = MP_TOTAL_4;
 
 // 4D generic orbit in the exact core: outputs per register group (24 / G)
 // and the CTAs per SM the kernel is compiled for
-// K2 CTA grouping: log2 of the tiles per coarse-block edge (3D / 4D)
+// K2 CTA grouping: log2 of the tiles per coarse-block edge (2D / 3D / 4D)
+#ifndef SS_K2_LF2
+#define SS_K2_LF2 0
+#endif
 #ifndef SS_K2_LF3
 #define SS_K2_LF3 1
 #endif
@@ -264,10 +267,13 @@ struct Launch {
 };
 
 // byte layout of a batch image for at most n problems: KParams[n], then the
-// prefix segments (n + 8 int64), then the vector widths (n int)
+// prefix segments (n + BATCH_MAX_CLASSES int64), then the vector widths (n int)
 constexpr size_t batch_offset_probs(int n) { return (void)n, 0; }
 constexpr size_t batch_offset_prefix(int n) { return sizeof(KParams) * (size_t)n; }
-constexpr size_t batch_offset_vec(int n) { return batch_offset_prefix(n) + sizeof(int64_t) * (size_t)(n + 8); }
+constexpr int BATCH_MAX_CLASSES = 12;  // (d, arithmetic) classes: 3 x 3, with room
+constexpr size_t batch_offset_vec(int n) {
+  return batch_offset_prefix(n) + sizeof(int64_t) * (size_t)(n + BATCH_MAX_CLASSES);
+}
 constexpr size_t batch_image_bytes(int n) { return batch_offset_vec(n) + sizeof(int) * (size_t)n; }
 
 // device image of a batch (plan memory, or the library's fixed array): the

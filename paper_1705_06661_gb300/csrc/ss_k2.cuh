@@ -35,6 +35,23 @@ namespace ss {
 template <int D>
 struct K2Shape;
 template <>
+struct K2Shape<2> {
+  static constexpr int BL = 32, NT = 1024;  // 32 x 32 tiles: 256-byte rows
+  // the pair index c0 / 2 is XORed with c1 mod 16
+  __device__ static __forceinline__ int phys(const int (&c)[4]) {
+    return ((((c[0] >> 1) ^ (c[1] & 15)) << 1) | (c[0] & 1)) + 32 * c[1];
+  }
+  // warp e / 32 takes the 16 x 2 block ((e >> 5) & 1, e >> 6) of the tile,
+  // lane l its element (l & 15, l >> 4)
+  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+    const int l = e & 31, b = e >> 5;
+    w[0] = (l & 15) + 16 * (b & 1);
+    w[1] = (l >> 4) + 2 * (b >> 1);
+    w[2] = 0;
+    w[3] = 0;
+  }
+};
+template <>
 struct K2Shape<3> {
   static constexpr int BL = 8, NT = 512;  // tile edge, elements per tile
   // shared-memory place of in-tile offset c: the pair index c0 / 2 is XORed
@@ -156,7 +173,7 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
 // as a pattern index of ss_internal.h; a packed table, not a local-memory array
 template <int D>
 __device__ __forceinline__ int k2_elem_pattern(unsigned eq) {
-  if constexpr (D == 3) {
+  if constexpr (D <= 3) {  // d = 2: bit 0 = (0,1) equal
     return (int)eq;
   } else {
     return (int)((0x76435210u >> (4 * eq)) & 0xFu);  // eq 0..7 -> 0 1 2 5 3 4 6 7
@@ -168,8 +185,8 @@ __device__ __forceinline__ void k2_dispatch(const KParams& kp, int ep, const int
   switch (ep) {
     case 0: if constexpr (kK2Map<D, BP, 0>.valid) k2_group<D, BP, 0, AR, T>(kp, w, sm); break;
     case 1: if constexpr (kK2Map<D, BP, 1>.valid) k2_group<D, BP, 1, AR, T>(kp, w, sm); break;
-    case 2: if constexpr (kK2Map<D, BP, 2>.valid) k2_group<D, BP, 2, AR, T>(kp, w, sm); break;
-    case 3: if constexpr (kK2Map<D, BP, 3>.valid) k2_group<D, BP, 3, AR, T>(kp, w, sm); break;
+    case 2: if constexpr (npatterns(D) > 2) { if constexpr (kK2Map<D, BP, 2>.valid) k2_group<D, BP, 2, AR, T>(kp, w, sm); } break;
+    case 3: if constexpr (npatterns(D) > 3) { if constexpr (kK2Map<D, BP, 3>.valid) k2_group<D, BP, 3, AR, T>(kp, w, sm); } break;
     default:
       if constexpr (D == 4) {
         switch (ep) {
@@ -309,8 +326,8 @@ __device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t s
     switch (k2_elem_pattern<D>(eq)) {
       case 0: k2_fill<D, 0>(kp, val, dsc); break;
       case 1: k2_fill<D, 1>(kp, val, dsc); break;
-      case 2: k2_fill<D, 2>(kp, val, dsc); break;
-      case 3: k2_fill<D, 3>(kp, val, dsc); break;
+      case 2: if constexpr (npatterns(D) > 2) k2_fill<D, 2>(kp, val, dsc); break;
+      case 3: if constexpr (npatterns(D) > 3) k2_fill<D, 3>(kp, val, dsc); break;
       default:
         if constexpr (D == 4) {
           switch (k2_elem_pattern<D>(eq)) {
@@ -444,8 +461,8 @@ __device__ __forceinline__ void k2_compute(const KParams& kp, const K2Desc& dsc,
   switch (dsc.bp) {
     case 0: k2_orbits<D, 0, AR, T>(kp, dsc, sm); break;
     case 1: k2_orbits<D, 1, AR, T>(kp, dsc, sm); break;
-    case 2: k2_orbits<D, 2, AR, T>(kp, dsc, sm); break;
-    case 3: k2_orbits<D, 3, AR, T>(kp, dsc, sm); break;
+    case 2: if constexpr (npatterns(D) > 2) k2_orbits<D, 2, AR, T>(kp, dsc, sm); break;
+    case 3: if constexpr (npatterns(D) > 3) k2_orbits<D, 3, AR, T>(kp, dsc, sm); break;
     default:
       if constexpr (D == 4) {
         switch (dsc.bp) {
@@ -520,9 +537,9 @@ __global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ K
 // the register budget.
 template <int D, int AR, int U, typename T>
 cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
-  constexpr int NBUF = D == 3 ? SS_K2_NBUF3 : SS_K2_NBUF4;
-  constexpr int MINB = D == 3 ? SS_K2_MINB3 : SS_K2_MINB4;
-  constexpr int RUN = D == 3 ? SS_K2_RUN3 : SS_K2_RUN4;
+  constexpr int NBUF = D <= 3 ? SS_K2_NBUF3 : SS_K2_NBUF4;
+  constexpr int MINB = D <= 3 ? SS_K2_MINB3 : SS_K2_MINB4;
+  constexpr int RUN = D <= 3 ? SS_K2_RUN3 : SS_K2_RUN4;
   constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
   auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
   constexpr int MAXDEV = 64;

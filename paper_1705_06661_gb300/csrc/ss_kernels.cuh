@@ -501,8 +501,8 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   switch (p) {
     case 0: k1_body<D, 0, AR, VEC, T>(kp, orb, c0, c1); break;
     case 1: k1_body<D, 1, AR, VEC, T>(kp, orb, c0, c1); break;
-    case 2: k1_body<D, 2, AR, VEC, T>(kp, orb, c0, c1); break;
-    case 3: k1_body<D, 3, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 2: if constexpr (npatterns(D) > 2) k1_body<D, 2, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 3: if constexpr (npatterns(D) > 3) k1_body<D, 3, AR, VEC, T>(kp, orb, c0, c1); break;
     default:
       if constexpr (D == 4) {
         switch (p) {
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? SS_4D_MINBLO
 // ---------------------------------------------------------------------------
 template <int D, int AR, typename T>
 __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int64_t b) {
-  constexpr int VMAX = sizeof(T) == 8 ? (D == 3 ? 2 : 1) : (D == 3 ? 4 : 1);
+  constexpr int VMAX = sizeof(T) == 8 ? (D <= 3 ? 2 : 1) : (D <= 3 ? 4 : 1);
   if constexpr (VMAX >= 4) {
     if (vec == 4) { k1_block<D, AR, 4, T>(kp, b); return; }
   }
@@ -540,7 +540,7 @@ __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int6
 }
 
 template <int D, int AR, typename T>
-__global__ void __launch_bounds__(256, D == 3 ? SS_KB_MINB3 : 1) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
+__global__ void __launch_bounds__(256, D <= 3 ? SS_KB_MINB3 : 1) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
                                                  const int* __restrict__ vecs, int n) {
   __shared__ KParams skp;
   const int64_t total = prefix[n];
@@ -615,8 +615,8 @@ __global__ void __launch_bounds__(256) kg_kernel(const __grid_constant__ KParams
   switch (p) {
     case 0: kg_body<D, 0, AR, T>(kp, lg); break;
     case 1: kg_body<D, 1, AR, T>(kp, lg); break;
-    case 2: kg_body<D, 2, AR, T>(kp, lg); break;
-    case 3: kg_body<D, 3, AR, T>(kp, lg); break;
+    case 2: if constexpr (npatterns(D) > 2) kg_body<D, 2, AR, T>(kp, lg); break;
+    case 3: if constexpr (npatterns(D) > 3) kg_body<D, 3, AR, T>(kp, lg); break;
     default:
       if constexpr (D == 4) {
         switch (p) {

@@ -1,5 +1,6 @@
 // Device status word and the dispatch from (d, arithmetic, vector width) to
-// the kernel instantiations of the ss_k1_*, ss_kg_* and ss_kb_* translation units.
+// the kernel instantiations of the ss_k1_*, ss_k2_*, ss_kg_* and ss_kb_*
+// translation units.
 #include <cuda_runtime.h>
 
 #include "ss_internal.h"
@@ -8,6 +9,11 @@ namespace ss {
 
 __device__ int g_status;
 
+cudaError_t launch_k1_d2(const KParams& kp, int ar, int vec, cudaStream_t st);
+cudaError_t launch_kg_d2(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_k2_d2(const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_kb_d2(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+                         cudaStream_t st, const void** fn);
 cudaError_t launch_k1_d3(const KParams& kp, int ar, int vec, cudaStream_t st);
 cudaError_t launch_k1_d4_exact(const KParams& kp, cudaStream_t st);
 cudaError_t launch_k1_d4_strict(const KParams& kp, cudaStream_t st);
@@ -29,6 +35,7 @@ cudaError_t launch_kb_d4_f32(const KParams* probs, const int64_t* prefix, const 
                               cudaStream_t st, const void** fn);
 
 cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st) {
+  if (d == 2) return launch_k1_d2(kp, ar, vec, st);
   if (d == 3) return launch_k1_d3(kp, ar, vec, st);
   if (ar == AR_EXACT) return launch_k1_d4_exact(kp, st);
   if (ar == AR_STRICT) return launch_k1_d4_strict(kp, st);
@@ -62,6 +69,7 @@ int* status_ptr() {
 
 // tiled kernel for the paper's N^d layout
 cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st) {
+  if (d == 2) return launch_k2_d2(kp, ar, st);
   if (d == 3) return launch_k2_d3(kp, ar, st);
   if (ar == AR_EXACT) return launch_k2_d4_exact(kp, st);
   if (ar == AR_STRICT) return launch_k2_d4_strict(kp, st);
@@ -69,12 +77,14 @@ cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st) {
 }
 
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st) {
+  if (d == 2) return launch_kg_d2(kp, ar, st);
   return d == 3 ? launch_kg_d3(kp, ar, st) : launch_kg_d4(kp, ar, st);
 }
 
 // batched kernel of class (d, ar); with fn != nullptr only reports the kernel symbol
 cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
                       cudaStream_t st, const void** fn) {
+  if (d == 2) return launch_kb_d2(ar, probs, prefix, vecs, n, grid, st, fn);
   if (d == 3) return launch_kb_d3(ar, probs, prefix, vecs, n, grid, st, fn);
   if (ar == AR_EXACT) return launch_kb_d4_exact(probs, prefix, vecs, n, grid, st, fn);
   if (ar == AR_STRICT) return launch_kb_d4_strict(probs, prefix, vecs, n, grid, st, fn);

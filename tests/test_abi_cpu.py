@@ -34,7 +34,8 @@ def header_functions():
 
 def test_exports_every_declared_function(lib):
     names = header_functions()
-    assert "spinsum_3d" in names and "spinsum_4d" in names and "spinsum_plan_create" in names
+    assert "spinsum_2d" in names and "spinsum_3d" in names and "spinsum_4d" in names
+    assert "spinsum_plan_create" in names
     for n in names:
         assert hasattr(lib, n), n
 
@@ -151,7 +152,7 @@ def test_host_product_rule_matches_oracle(lib, row):
 
 def test_host_product_rule_random_chains(lib):
     import oracle
-    for d in (3, 4):
+    for d in (2, 3, 4):
         chain = np.concatenate([wl.random_coef(d, 300 + d), wl.random_coef(d, 310 + d), wl.uniform(320, (1, math.factorial(d)))])
         ex, info, _, _ = debug_plan(lib, d, 4, 4, chain, mode=1)
         np.testing.assert_array_equal(ex, oracle.expand(d, chain))
@@ -159,13 +160,14 @@ def test_host_product_rule_random_chains(lib):
         assert info["nstage"] == 3
 
 
-@pytest.mark.parametrize("d,O", [(3, 1), (3, 2), (3, 5), (3, 16), (4, 1), (4, 3), (4, 5), (4, 12), (4, 40)])
+@pytest.mark.parametrize("d,O", [(2, 1), (2, 7), (2, 64), (3, 1), (3, 2), (3, 5), (3, 16), (4, 1), (4, 3), (4, 5),
+                                 (4, 12), (4, 40)])
 def test_orbit_counts(lib, d, O):
     """orbits per equality pattern are the choices of distinct values; the
     orbit members cover the O^d tuples exactly once."""
     _, info, _, _ = debug_plan(lib, d, O, 8, wl.random_coef(d, 1))
     norb = info["norb"]
-    sizes = [6, 3, 3, 1] if d == 3 else [24, 12, 12, 12, 6, 4, 4, 1]
+    sizes = {2: [2, 1], 3: [6, 3, 3, 1], 4: [24, 12, 12, 12, 6, 4, 4, 1]}[d]
     assert sum(n * m for n, m in zip(norb, sizes)) == O ** d
     # canonical tuples i <= j <= k (<= l): C(O + d - 1, d)
     assert sum(norb[:len(sizes)]) == math.comb(O + d - 1, d)
@@ -176,11 +178,11 @@ def test_orbit_counts(lib, d, O):
 def test_orbit_matrices(lib):
     """rows of every degenerate pattern's orbit matrix sum to sum(alpha);
     the 1-member pattern's matrix is exactly sum(alpha)."""
-    for d in (3, 4):
+    for d in (2, 3, 4):
         a = wl.random_coef(d, 400 + d)
         _, info, ci, mp = debug_plan(lib, d, 6, 8, a)
         np.testing.assert_array_equal(ci[0, :math.factorial(d)], a[0].astype(np.int32))
-        sizes = [6, 3, 3, 1] if d == 3 else [24, 12, 12, 12, 6, 4, 4, 1]
+        sizes = {2: [2, 1], 3: [6, 3, 3, 1], 4: [24, 12, 12, 12, 6, 4, 4, 1]}[d]
         off = 0
         for m in sizes[1:]:
             M = mp[off:off + m * m].reshape(m, m)
@@ -225,8 +227,9 @@ def test_launch_shape(lib):
     assert info["kernel"] == 1
     # the paper's N^d layout (no spectators, first permuted index at stride 1): tiled kernel
     # CTAs: F^d per sorted tuple of coarse blocks (F tiles per coarse edge)
-    for d, N, bl in ((3, 344, 8), (4, 80, 4)):
-        _, info, _, _ = debug_plan(lib, d, N, 1, wl.table2(1 if d == 3 else 5))
+    for d, N, bl in ((2, 1000, 32), (3, 344, 8), (4, 80, 4)):
+        coef = {2: np.array([[2.0, -1.0]]), 3: wl.table2(1), 4: wl.table2(5)}[d]
+        _, info, _, _ = debug_plan(lib, d, N, 1, coef)
         F = 1 << info["k2lf"]
         nc = -(-(-(-N // bl)) // F)
         assert info["kernel"] == 3 and info["blocks"] == math.comb(nc + d - 1, d) * F ** d

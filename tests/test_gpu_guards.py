@@ -53,7 +53,7 @@ def _check_guards(buf, mask, msg):
 
 
 CASES = [
-    # name, d, shape, coef row (0: random set), factorized, dtype, guard, strides-kind
+    # name, d, shape, coef row (0: random set, -1: the d = 2 set 2, -1), factorized, dtype, guard, strides-kind
     ("k1 3d 16-byte runs", 3, (6, 6, 6, 8, 8, 8), 1, True, "f64", 4096, None),
     ("k1 3d misaligned runs", 3, (6, 6, 6, 8, 8, 8), 1, True, "f64", 4097, None),
     ("k1 3d odd spectator block", 3, (5, 5, 5, 7, 7, 7), 2, False, "f64", 4096, None),
@@ -66,6 +66,10 @@ CASES = [
     ("k2 4d ragged", 4, (9, 9, 9, 9), 6, True, "f64", 4096, None),
     ("k2 4d fp32", 4, (10, 10, 10, 10), 5, True, "f32", 4096, None),
     ("kg sliced spectators", 3, (4, 4, 4, 6, 6, 6), 1, True, "f64", 4096, "gaps"),
+    ("k1 2d", 2, (24, 24, 20, 20), -1, False, "f64", 4096, None),
+    ("k1 2d misaligned", 2, (24, 24, 20, 20), -1, False, "f64", 4097, None),
+    ("k2 2d ragged", 2, (70, 70), -1, False, "f64", 4096, None),
+    ("k2 2d ragged scalar copies", 2, (45, 45), -1, False, "f32", 4097, None),
 ]
 
 
@@ -77,7 +81,7 @@ def test_writes_stay_inside(case, mode):
     import paper_1705_06661_gb300 as ss
     name, d, shape, row, fac, dt, guard, sk = case
     tdt = torch.float64 if dt == "f64" else torch.float32
-    coef = wl.table2(row) if row else wl.random_coef(d, 77)
+    coef = np.array([[2.0, -1.0]]) if row < 0 else (wl.table2(row) if row else wl.random_coef(d, 77))
     A_np = wl.uniform(31, shape)
     if dt == "f32":
         A_np = A_np.astype(np.float32).astype(np.float64)

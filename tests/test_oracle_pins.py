@@ -415,3 +415,22 @@ def test_table2_flop_reduction_factors(oracle_mod):
         counts[row] = (adds_exp, adds_fac)
     assert len({counts[r] for r in range(6, 18)}) == 1
     assert max(counts, key=lambda r: counts[r][0] / counts[r][1]) == 5
+
+
+def test_d2_is_a_weighted_transpose(oracle_mod):
+    """d = 2 (Def. 3 with the two permutations of (i, j)): B = a_12 A +
+    a_21 A^T over the permuted pair, against numpy's transpose, with
+    spectators and on the plain N^2 matrix; a two-factor chain equals its
+    product (the group algebra of S_2: (a + b t)(c + e t) = (ac + be) + (ae + bc) t)."""
+    A = wl.uniform(61, (3, 4, 6, 6))
+    for coef in ([1.0, 1.0], [1.0, -1.0], [2.0, -1.0], [0.0, 1.0]):
+        want = coef[0] * A + coef[1] * A.transpose(0, 1, 3, 2)
+        np.testing.assert_array_equal(oracle_mod.spinsum(A, 2, np.array([coef])), want)
+    M = wl.uniform(62, (9, 9))
+    np.testing.assert_array_equal(oracle_mod.spinsum(M, 2, np.array([[3.0, -2.0]])), 3.0 * M - 2.0 * M.T)
+    chain = np.array([[2.0, -1.0], [1.0, 3.0]])
+    a, b, c, e = 2.0, -1.0, 1.0, 3.0
+    np.testing.assert_array_equal(oracle_mod.expand(2, chain), [a * c + b * e, a * e + b * c])
+    Ai = wl.integers(63, (5, 5, 7, 7))
+    np.testing.assert_array_equal(oracle_mod.spinsum(Ai, 2, chain, factorized=True),
+                                  oracle_mod.spinsum(Ai, 2, chain, factorized=False))
