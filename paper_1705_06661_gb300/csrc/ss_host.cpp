@@ -247,7 +247,8 @@ int plan_one(const Request& r, Launch* L) {
   const int O = (int)r.ext[d];
   for (int k = d; k < nidx; k++)
     if (r.ext[k] != r.ext[d]) return fail(SPINSUM_ERR_ARG, "permuted extents must be equal (index %d)", k);
-  if (r.ext[d] > 4096) return fail(SPINSUM_ERR_UNSUPPORTED, "permuted extent above 4096");
+  const int64_t omax = d == 2 ? 65536 : 4096;
+  if (r.ext[d] > omax) return fail(SPINSUM_ERR_UNSUPPORTED, "permuted extent above %lld", (long long)omax);
   const Group& g = group(d);
   for (int i = 0; i < r.nfactors * g.n; i++)
     if (!std::isfinite(r.coef[i])) return fail(SPINSUM_ERR_ARG, "non-finite coefficient at %d", i);

@@ -160,6 +160,15 @@ constexpr int MP_MAX = MP_TOTAL_4;
 // K2: buffers of d! tiles per CTA (2 = the next block orbit is copied while the
 // current one is computed) and resident CTAs per SM the register budget is
 // sized for
+#ifndef SS_K2_NBUF2
+#define SS_K2_NBUF2 2
+#endif
+#ifndef SS_K2_RUN2
+#define SS_K2_RUN2 4
+#endif
+#ifndef SS_K2_MINB2
+#define SS_K2_MINB2 4
+#endif
 #ifndef SS_K2_NBUF3
 #define SS_K2_NBUF3 2
 #endif

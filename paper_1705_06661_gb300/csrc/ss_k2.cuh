@@ -531,15 +531,14 @@ __global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ K
   }
 }
 
-// Launch shape: SS_K2_NBUF3 / SS_K2_NBUF4 buffers of d! dense tiles per CTA,
-// SS_K2_RUN3 / SS_K2_RUN4 consecutive ids per CTA (0: a persistent grid of
-// the resident CTAs) and SS_K2_MINB3 / SS_K2_MINB4 resident CTAs per SM for
-// the register budget.
+// Launch shape per d: SS_K2_NBUF<d> buffers of d! dense tiles per CTA,
+// SS_K2_RUN<d> consecutive ids per CTA (0: a persistent grid of the resident
+// CTAs) and SS_K2_MINB<d> resident CTAs per SM for the register budget.
 template <int D, int AR, int U, typename T>
 cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
-  constexpr int NBUF = D <= 3 ? SS_K2_NBUF3 : SS_K2_NBUF4;
-  constexpr int MINB = D <= 3 ? SS_K2_MINB3 : SS_K2_MINB4;
-  constexpr int RUN = D <= 3 ? SS_K2_RUN3 : SS_K2_RUN4;
+  constexpr int NBUF = D == 2 ? SS_K2_NBUF2 : (D == 3 ? SS_K2_NBUF3 : SS_K2_NBUF4);
+  constexpr int MINB = D == 2 ? SS_K2_MINB2 : (D == 3 ? SS_K2_MINB3 : SS_K2_MINB4);
+  constexpr int RUN = D == 2 ? SS_K2_RUN2 : (D == 3 ? SS_K2_RUN3 : SS_K2_RUN4);
   constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
   auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
   constexpr int MAXDEV = 64;
