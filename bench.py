@@ -487,6 +487,23 @@ def run_ours(args):
                           "ms_single_launch": round(one * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
         del A4, B4
         torch.cuda.empty_cache()
+        # d = 2 (the CCSD pair, coefficients 2, -1): spectator layout and the N^2 matrix
+        for shp2, nm in (((96, 96, 96, 96), "2d A[96^4]"), ((8192, 8192), "paper layout 2d N=8192")):
+            A2 = ss.colmajor_empty(shp2, device=dev)
+            A2.copy_(torch.from_numpy(wl.uniform(3, shp2)).to(dev))
+            B2 = ss.colmajor_like(A2)
+            c2 = np.array([[2.0, -1.0]])
+            for name, fn in ((f"{nm} (2,-1) out-of-place", lambda: ss.spinsum(A2, c2, d=2, out=B2)),
+                             (f"{nm} (2,-1) in-place (alpha=0.5)",
+                              lambda: ss.spinsum(A2, c2, d=2, inplace=True, alpha=0.5))):
+                for _ in range(2):
+                    fn()
+                mn, one = best_of(fn, reps, stream)
+                n2 = A2.numel()
+                extra.append({"case": name, "GB/s": round(2 * n2 * 8 / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                              "frac": round(2 * n2 * 8 / mn / 1e9 / hbm_peak, 4)})
+            del A2, B2
+            torch.cuda.empty_cache()
         # the paper's own layout: a dense N^d tensor with every index permuted (tiled kernel)
         for dp, Np, rowp in ((3, 544, 1), (4, 112, 5)):
             shp = (Np,) * dp
