@@ -1,4 +1,4 @@
-"""Host-resident tensors (spinsum_3d_host / spinsum_4d_host): chunked,
+"""Host-resident tensors (spinsum_2d_host / spinsum_3d_host / spinsum_4d_host): chunked,
 pipelined copy-in / sum / copy-out against the oracle, with pinned and
 pageable memory, in place, with beta, and with a workspace of one slice."""
 import numpy as np
@@ -22,12 +22,12 @@ def _cpu(A_np, pinned):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-@pytest.mark.parametrize("d,shape", [(3, (6, 5, 9, 5, 5, 5)), (4, (3, 4, 2, 5, 4, 4, 4, 4))])
+@pytest.mark.parametrize("d,shape", [(2, (9, 7, 11, 11)), (3, (6, 5, 9, 5, 5, 5)), (4, (3, 4, 2, 5, 4, 4, 4, 4))])
 def test_host_pipeline_matches_oracle(d, shape, pinned):
     import torch
     import oracle
     import paper_1705_06661_gb300 as ss
-    coef = wl.table2(1 if d == 3 else 5)
+    coef = {2: np.array([[2.0, -1.0]]), 3: wl.table2(1), 4: wl.table2(5)}[d]
     for kind in ("int", "uni"):
         A_np = (wl.integers if kind == "int" else wl.uniform)(31, shape)
         want = oracle.spinsum(A_np, d, coef, factorized=True)
