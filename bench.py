@@ -94,7 +94,7 @@ class ClockSampler:
             self.samples.append((time.time(), line.strip()))
 
     def wait_first_sample(self, timeout: float = 10.0):
-        """nvidia-smi's start-up can hold the driver for a while; time nothing
+        """nvidia-smi's start-up can hold the GPU for a while; time nothing
         before its first sample has arrived."""
         t0 = time.time()
         while self.proc and not self.samples and time.time() - t0 < timeout:
