@@ -152,8 +152,8 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
     auto sink = [&](int u, double v) { sm[s[u]] = v; };
     if (exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) {
       if (kp.flags & KF_ALPHA_MUL) {  // alpha not a power of two: rare, a separate pass
-#pragma unroll 1
-        for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, sm[s[u]]);
+#pragma unroll
+        for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, sm[s[u]]);  // unrolled: s stays in registers
       }
       return;
     }
