@@ -149,6 +149,37 @@ int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_
                     int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
 
 /*
+ * Packed antisymmetric storage (tensor unpacking, named in Sec. 2 and Sec. 6
+ * as a further use of the orbit traversal). An antisymmetric tensor B over
+ * its d permuted indices is stored as P[s, r]: one value per strictly
+ * increasing tuple t0 = (i_1 < .. < i_d), r = sum_k C(i_k, k + 1) (the colex
+ * rank), C(O, d) values per spectator position s.
+ *
+ * spinsum_unpack -- B[s, t0 o tau] = sign(tau) * P[s, r] for every
+ *   permutation tau, and B[s, t] = 0 where t repeats an index. Writes all of B.
+ * spinsum_pack -- P[s, r] = B[s, t0] (the canonical member): the inverse of
+ *   unpack on antisymmetric tensors.
+ *
+ * d      : 2, 3 or 4.
+ * dtype  : SPINSUM_F64 or SPINSUM_F32 (P and B alike).
+ * ext    : 2d extents of B: d spectators, then d permuted extents (equal, O).
+ * B, ldb : the full tensor and its 2d element strides; the spectator indices
+ *          must be dense and fastest (stride 1, then products of extents).
+ * P, ldp : the packed tensor and its d + 1 element strides: the d spectator
+ *          strides (equal to B's) and the stride of the packed index
+ *          (at least the spectator block).
+ * stream : cudaStream_t to launch on.
+ * Errors: SPINSUM_ERR_ARG (bad d, dtype, extents or strides),
+ * SPINSUM_ERR_UNSUPPORTED (non-dense spectators, O > 4096),
+ * SPINSUM_ERR_ALIAS (P and B overlap), SPINSUM_ERR_CUDA. Caller-owned memory;
+ * nothing is allocated; asynchronous on `stream`.
+ */
+int spinsum_unpack(int d, int dtype, const int64_t ext[], const void* P, const int64_t ldp[], void* B,
+                   const int64_t ldb[], spinsum_stream_t stream);
+int spinsum_pack(int d, int dtype, const int64_t ext[], const void* B, const int64_t ldb[], void* P,
+                 const int64_t ldp[], spinsum_stream_t stream);
+
+/*
  * Batched plans: many independent spin summations (uneven extents, mixed d,
  * mixed coefficient sets) run by one persistent kernel launch.
  *

@@ -11,6 +11,10 @@ permuted index group, the leading axes are spectators. Coefficient chains are
 arrays of shape [nfactors, d!] in lexicographic permutation order, meaning
 B = F_1(F_2(...F_k(A))).
 
+Packed antisymmetric storage (``unpack`` / ``pack``) is written here in numpy
+from its definition: one value per strictly increasing tuple, indexed by its
+colex rank (the combinatorial number system), signs from the inversion count.
+
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (copy / single-permutation transposes against numpy's transpose, the paper's
 Eq. 7 = Eq. 8 factorization, the Sec. 4.6.2 regularization identity, the
@@ -134,3 +138,39 @@ def spinsum_transpose(Y: np.ndarray, d: int, coef, alpha: float = 1.0) -> np.nda
     if rc != 0:
         raise ValueError(f"oracle_spinsum_transpose failed ({rc})")
     return X
+
+
+def colex_rank(t) -> int:
+    """Rank of the strictly increasing tuple t among all such tuples in colex
+    order: sum_k C(t_k, k + 1) (the combinatorial number system)."""
+    return int(sum(math.comb(int(x), k + 1) for k, x in enumerate(t)))
+
+
+def _inversions(t) -> int:
+    return sum(1 for a in range(len(t)) for b in range(a + 1, len(t)) if t[a] > t[b])
+
+
+def unpack(P: np.ndarray, d: int, O: int) -> np.ndarray:
+    """Antisymmetric tensor from its packed form: B[s, t] = (-1)^inv(t) *
+    P[s, rank(sorted t)] for t without repeated entries, else 0. P has the
+    spectator axes then one packed axis of length C(O, d)."""
+    import itertools
+    spec = P.shape[:-1]
+    B = np.zeros(spec + (O,) * d)
+    for t in itertools.product(range(O), repeat=d):
+        if len(set(t)) < d:
+            continue
+        sign = -1.0 if _inversions(t) % 2 else 1.0
+        B[(Ellipsis,) + t] = sign * P[..., colex_rank(sorted(t))]
+    return B
+
+
+def pack(B: np.ndarray, d: int) -> np.ndarray:
+    """Packed form: P[s, rank(t0)] = B[s, t0] for every strictly increasing t0."""
+    import itertools
+    O = B.shape[-1]
+    spec = B.shape[:-d]
+    P = np.zeros(spec + (math.comb(O, d),))
+    for t0 in itertools.combinations(range(O), d):
+        P[..., colex_rank(t0)] = B[(Ellipsis,) + t0]
+    return P

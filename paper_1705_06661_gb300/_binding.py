@@ -100,6 +100,10 @@ def _load() -> ctypes.CDLL:
     lib.spinsum_launch_count.restype = ctypes.c_int64
     lib.spinsum_version.argtypes = []
     lib.spinsum_version.restype = ctypes.c_char_p
+    lib.spinsum_unpack.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, _VP, _I64P, _VP, _I64P, _VP]
+    lib.spinsum_unpack.restype = ctypes.c_int
+    lib.spinsum_pack.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, _VP, _I64P, _VP, _I64P, _VP]
+    lib.spinsum_pack.restype = ctypes.c_int
     return lib
 
 
@@ -132,6 +136,22 @@ def _call(fn, n, dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, 
     c = _coef(coef)
     return _check(fn(int(dtype), _i64(ext), _VP(A), _i64(lda), _VP(B), _i64(ldb), _VP(c.ctypes.data),
                      int(nfactors), int(mode), float(alpha), float(beta), int(inplace), _VP(stream)))
+
+
+def spinsum_unpack(d, dtype, ext, P, ldp, B, ldb, stream) -> int:
+    """spinsum_unpack of the C-ABI; P, B and stream are integer addresses."""
+    if len(ext) != 2 * d or len(ldb) != 2 * d or len(ldp) != d + 1:
+        raise ValueError("expected 2d extents and B strides, d + 1 P strides")
+    return _check(lib.spinsum_unpack(int(d), int(dtype), _i64(ext), _VP(P), _i64(ldp), _VP(B), _i64(ldb),
+                                     _VP(stream)))
+
+
+def spinsum_pack(d, dtype, ext, B, ldb, P, ldp, stream) -> int:
+    """spinsum_pack of the C-ABI; B, P and stream are integer addresses."""
+    if len(ext) != 2 * d or len(ldb) != 2 * d or len(ldp) != d + 1:
+        raise ValueError("expected 2d extents and B strides, d + 1 P strides")
+    return _check(lib.spinsum_pack(int(d), int(dtype), _i64(ext), _VP(B), _i64(ldb), _VP(P), _i64(ldp),
+                                   _VP(stream)))
 
 
 def spinsum_2d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream) -> int:

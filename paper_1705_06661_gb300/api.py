@@ -129,6 +129,52 @@ def spinsum_host(A: torch.Tensor, coef, *, out: torch.Tensor | None = None, work
     return out
 
 
+def _dtype_code(x: torch.Tensor) -> int:
+    if x.dtype == torch.float64:
+        return _b.SPINSUM_F64
+    if x.dtype == torch.float32:
+        return _b.SPINSUM_F32
+    raise ValueError("dtype must be float64 or float32")
+
+
+def unpack(P: torch.Tensor, d: int, O: int, out: torch.Tensor | None = None,
+           stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Antisymmetric tensor B [spectators..., O, .., O] from its packed form P
+    [spectators..., C(O, d)] (spinsum_unpack): B[s, t0 o tau] = sign(tau) P[s, r],
+    r the colex rank of i_1 < .. < i_d; zero where an index repeats."""
+    if not P.is_cuda:
+        raise ValueError("P must be a CUDA tensor")
+    nspec = P.dim() - 1
+    if nspec != d:
+        raise ValueError(f"P needs {d} spectator dimensions and the packed one")
+    if P.shape[-1] != math.comb(O, d):
+        raise ValueError(f"packed extent must be C({O}, {d}) = {math.comb(O, d)}")
+    shape = tuple(P.shape[:d]) + (O,) * d
+    if out is None:
+        out = colmajor_empty(shape, dtype=P.dtype, device=P.device)
+    st = (stream or torch.cuda.current_stream(P.device)).cuda_stream
+    _b.spinsum_unpack(d, _dtype_code(P), list(shape), P.data_ptr(), list(P.stride()), out.data_ptr(),
+                      list(out.stride()), st)
+    return out
+
+
+def pack(B: torch.Tensor, d: int, out: torch.Tensor | None = None,
+         stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """Packed form P [spectators..., C(O, d)] of an antisymmetric tensor B
+    [spectators..., O, .., O] (spinsum_pack): P[s, r] = B[s, i_1 < .. < i_d]."""
+    if not B.is_cuda:
+        raise ValueError("B must be a CUDA tensor")
+    if B.dim() != 2 * d:
+        raise ValueError(f"B needs {2 * d} dimensions")
+    O = int(B.shape[d])
+    if out is None:
+        out = colmajor_empty(tuple(B.shape[:d]) + (math.comb(O, d),), dtype=B.dtype, device=B.device)
+    st = (stream or torch.cuda.current_stream(B.device)).cuda_stream
+    _b.spinsum_pack(d, _dtype_code(B), list(B.shape), B.data_ptr(), list(B.stride()), out.data_ptr(),
+                    list(out.stride()), st)
+    return out
+
+
 class SpinSumFunction(torch.autograd.Function):
     """Differentiable spin summation. The operator is linear, so the gradient
     of B = alpha S(A) is alpha S^T(gB), S^T = sum a_sigma pi_{sigma^-1} for one

@@ -22,6 +22,7 @@ cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st
 cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st);
+cudaError_t launch_pack(int d, const KParams& kp, bool unpack, bool f64, int vec, cudaStream_t st);
 int k1t_chunk(int d, int ar);
 
 int* status_ptr();
@@ -478,6 +479,70 @@ int plan_one(const Request& r, Launch* L) {
   return SPINSUM_OK;
 }
 
+// Packed antisymmetric storage: B (2d indices, dense spectators at stride 1)
+// and P (d spectator indices with B's dense strides, then the packed index
+// r = colex rank of i_1 < .. < i_d). unpack: P -> B, pack: B -> P.
+int run_pack(bool unpack, int d, int dtype, const int64_t* ext, const void* P, const int64_t* ldp, const void* B,
+             const int64_t* ldb, cudaStream_t st) {
+  t_err.clear();
+  if (d < 2 || d > 4) return fail(SPINSUM_ERR_ARG, "d must be 2, 3 or 4");
+  if (dtype != SPINSUM_F64 && dtype != SPINSUM_F32) return fail(SPINSUM_ERR_ARG, "unknown dtype %d", dtype);
+  if (!ext || !ldp || !ldb) return fail(SPINSUM_ERR_ARG, "null extent or stride array");
+  const size_t es = dtype == SPINSUM_F64 ? 8 : 4;
+  int64_t S = 1;
+  for (int k = 0; k < d; k++) {
+    if (ext[k] < 0) return fail(SPINSUM_ERR_ARG, "negative extent at index %d", k);
+    if (ext[k] != 1 && (ldb[k] != S || ldp[k] != S))
+      return fail(SPINSUM_ERR_UNSUPPORTED, "spectator indices must be dense and fastest in P and B");
+    S *= ext[k];
+  }
+  const int64_t O = ext[d];
+  for (int k = d; k < 2 * d; k++) {
+    if (ext[k] != O) return fail(SPINSUM_ERR_ARG, "permuted extents must be equal (index %d)", k);
+    if (ldb[k] < 0) return fail(SPINSUM_ERR_UNSUPPORTED, "negative strides are not supported");
+  }
+  if (O > 4096) return fail(SPINSUM_ERR_UNSUPPORTED, "permuted extent above 4096");
+  if (ldp[d] < S) return fail(SPINSUM_ERR_ARG, "packed-index stride below the spectator block");
+  const int64_t npack = binom((int)O, d);
+  if (S == 0 || O == 0) return SPINSUM_OK;
+  if (!P || !B) return fail(SPINSUM_ERR_ARG, "null tensor pointer");
+  // P and B must not overlap
+  uintptr_t plo = (uintptr_t)P, phi = plo + (uintptr_t)(((npack > 0 ? (npack - 1) * ldp[d] : 0) + S) * (int64_t)es);
+  uintptr_t blo = 0, bhi = 0;
+  span(2 * d, ext, ldb, B, es, &blo, &bhi);
+  if (npack > 0 && plo < bhi && blo < phi) return fail(SPINSUM_ERR_ALIAS, "P and B overlap");
+  KParams kp{};
+  kp.A = P;
+  kp.B = const_cast<void*>(B);
+  kp.S = S;
+  kp.O = (int)O;
+  kp.lda[0] = ldp[d];
+  for (int k = 0; k < d; k++) kp.ldb[k] = ldb[d + k];
+  const int np = npatterns(d);
+  for (int p = 0; p < np; p++) kp.norb[p] = (unpack || p == 0) ? binom((int)O, nd_of(d, p)) : 0;
+  const int want = 2;  // pairs: 16 bytes (FP64) or 8 bytes (FP32)
+  bool pair = S % want == 0 && (uintptr_t)P % (es * want) == 0 && (uintptr_t)B % (es * want) == 0 &&
+              ldp[d] % want == 0;
+  for (int k = d; k < 2 * d; k++) pair = pair && ldb[k] % want == 0;
+  const int vec = pair ? want : 1;
+  const int64_t per = 256LL * vec;
+  kp.nchunk = (S + per - 1) / per;
+  const int64_t cpb0 = std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+  const int64_t nbo = (kp.nchunk + cpb0 - 1) / cpb0;
+  kp.cpb = (int)((kp.nchunk + nbo - 1) / nbo);
+  const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;
+  kp.pre[0] = 0;
+  for (int p = 0; p < np; p++) kp.pre[p + 1] = kp.pre[p] + kp.norb[p] * bpo;
+  for (int p = np; p < 8; p++) kp.pre[p + 1] = kp.pre[p];
+  if (kp.pre[np] == 0) return SPINSUM_OK;
+  if (kp.pre[np] > 0x7FFFFFFFLL) return fail(SPINSUM_ERR_UNSUPPORTED, "problem too large for one launch");
+  kp.status = status_ptr();
+  cudaError_t e = launch_pack(d, kp, unpack, dtype == SPINSUM_F64, vec, st);
+  t_launches++;
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return SPINSUM_OK;
+}
+
 int run(const Request& r, cudaStream_t st) {
   t_err.clear();
   Launch L;
@@ -496,6 +561,16 @@ int run(const Request& r, cudaStream_t st) {
 }  // namespace
 
 extern "C" {
+
+int spinsum_unpack(int d, int dtype, const int64_t ext[], const void* P, const int64_t ldp[], void* B,
+                   const int64_t ldb[], spinsum_stream_t stream) {
+  return run_pack(true, d, dtype, ext, P, ldp, B, ldb, (cudaStream_t)stream);
+}
+
+int spinsum_pack(int d, int dtype, const int64_t ext[], const void* B, const int64_t ldb[], void* P,
+                 const int64_t ldp[], spinsum_stream_t stream) {
+  return run_pack(false, d, dtype, ext, P, ldp, B, ldb, (cudaStream_t)stream);
+}
 
 int spinsum_2d(int dtype, const int64_t ext[4], const void* A, const int64_t lda[4], void* B,
                const int64_t ldb[4], const double* coef, int nfactors, int mode, double alpha, double beta,

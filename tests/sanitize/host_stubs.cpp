@@ -10,6 +10,7 @@ cudaError_t launch_k1(int, const KParams&, int, int, cudaStream_t) { return cuda
 cudaError_t launch_k1t(int, const KParams&, int, cudaStream_t) { return cudaErrorNoDevice; }
 cudaError_t launch_k2(int, const KParams&, int, cudaStream_t) { return cudaErrorNoDevice; }
 cudaError_t launch_kg(int, const KParams&, int, cudaStream_t) { return cudaErrorNoDevice; }
+cudaError_t launch_pack(int, const KParams&, bool, bool, int, cudaStream_t) { return cudaErrorNoDevice; }
 cudaError_t launch_kb(int, int, const KParams*, const int64_t*, const int*, int, int, cudaStream_t, const void**) {
   return cudaErrorNoDevice;
 }

@@ -434,3 +434,26 @@ def test_d2_is_a_weighted_transpose(oracle_mod):
     Ai = wl.integers(63, (5, 5, 7, 7))
     np.testing.assert_array_equal(oracle_mod.spinsum(Ai, 2, chain, factorized=True),
                                   oracle_mod.spinsum(Ai, 2, chain, factorized=False))
+
+
+@pytest.mark.parametrize("d,O", [(2, 7), (3, 6), (4, 6)])
+def test_packed_antisymmetric_storage(oracle_mod, d, O):
+    """unpack gives an antisymmetric tensor (any transposition of two permuted
+    axes negates it, equal indices give 0), pack inverts it, and the packed
+    axis has C(O, d) entries in colex order: for d = 2 the pair i < j sits at
+    i + j (j - 1) / 2 (C(i, 1) + C(j, 2), written out)."""
+    P = wl.uniform(90 + d, (3, 2, math.comb(O, d)))
+    B = oracle_mod.unpack(P, d, O)
+    nspec = B.ndim - d
+    for a, b in itertools.combinations(range(d), 2):
+        axes = list(range(B.ndim))
+        axes[nspec + a], axes[nspec + b] = axes[nspec + b], axes[nspec + a]
+        np.testing.assert_array_equal(B.transpose(axes), -B)
+    np.testing.assert_array_equal(oracle_mod.pack(B, d), P)
+    assert sorted(oracle_mod.colex_rank(t) for t in itertools.combinations(range(O), d)) == list(range(math.comb(O, d)))
+    if d == 2:
+        for i in range(O):
+            assert np.all(B[..., i, i] == 0)
+            for j in range(i + 1, O):
+                np.testing.assert_array_equal(B[..., i, j], P[..., i + j * (j - 1) // 2])
+                np.testing.assert_array_equal(B[..., j, i], -P[..., i + j * (j - 1) // 2])
