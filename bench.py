@@ -487,6 +487,21 @@ def run_ours(args):
                           "ms_single_launch": round(one * 1e3, 4), "frac": round(2 * n4 * 8 / mn / 1e9 / hbm_peak, 4)})
         del A4, B4
         torch.cuda.empty_cache()
+        # packed antisymmetric storage: the 3D tensor unpacked from its C(16, 3) = 560 values per position
+        Pk = ss.colmajor_empty((48, 48, 48, 560), device=dev)
+        Pk.copy_(torch.from_numpy(wl.uniform(5, (48, 48, 48, 560))).to(dev))
+        Bk = ss.colmajor_empty(SHAPE, device=dev)
+        for name, fn, nb in (("unpack 3d A[48^3, C(16,3)] -> A[48^3,16^3]", lambda: ss.unpack(Pk, 3, 16, out=Bk),
+                              (Pk.numel() + Bk.numel()) * 8),
+                             ("pack 3d A[48^3,16^3] -> A[48^3, C(16,3)]", lambda: ss.pack(Bk, 3, out=Pk),
+                              2 * Pk.numel() * 8)):
+            for _ in range(2):
+                fn()
+            mn, one = best_of(fn, reps, stream)
+            extra.append({"case": name, "GB/s": round(nb / mn / 1e9, 1), "ms": round(mn * 1e3, 4),
+                          "frac": round(nb / mn / 1e9 / hbm_peak, 4)})
+        del Pk, Bk
+        torch.cuda.empty_cache()
         # d = 2 (the CCSD pair, coefficients 2, -1): spectator layout and the N^2 matrix
         for shp2, nm in (((96, 96, 96, 96), "2d A[96^4]"), ((8192, 8192), "paper layout 2d N=8192")):
             A2 = ss.colmajor_empty(shp2, device=dev)
