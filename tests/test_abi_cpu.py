@@ -233,3 +233,37 @@ def test_launch_shape(lib):
         F = 1 << info["k2lf"]
         nc = -(-(-(-N // bl)) // F)
         assert info["kernel"] == 3 and info["blocks"] == math.comb(nc + d - 1, d) * F ** d
+
+
+@pytest.mark.parametrize("case,code", [("bad_d", -1), ("bad_dtype", -1), ("unequal_extents", -1),
+                                       ("sparse_spectators", -3), ("short_packed_stride", -1),
+                                       ("overlap", -2), ("extent_too_large", -3)])
+def test_pack_argument_errors_need_no_gpu(ss, case, code):
+    """spinsum_unpack / spinsum_pack validate before touching a device."""
+    d = 3
+    ext = [3, 3, 3, 6, 6, 6]
+    ldb = _dense(ext)
+    S = 27
+    ldp = [1, 3, 9, S]
+    P, B = FAKE_A, FAKE_B
+    dtype = ss.SPINSUM_F64
+    if case == "bad_d":
+        d, ext, ldb, ldp = 5, ext + [6, 6, 6, 6], _dense(ext + [6, 6, 6, 6]), ldp + [1, 1]
+    elif case == "bad_dtype":
+        dtype = 7
+    elif case == "unequal_extents":
+        ext[5] = 5
+    elif case == "sparse_spectators":
+        ldb[1] = 4
+    elif case == "short_packed_stride":
+        ldp[3] = S - 1
+    elif case == "overlap":
+        B = P + 8 * 10
+    elif case == "extent_too_large":
+        ext[3] = ext[4] = ext[5] = 5000
+        ldb = _dense(ext)
+    for fn in (lambda: ss.spinsum_unpack(d, dtype, ext, P, ldp, B, ldb, 0),
+               lambda: ss.spinsum_pack(d, dtype, ext, B, ldb, P, ldp, 0)):
+        with pytest.raises(ss.SpinsumError) as e:
+            fn()
+        assert e.value.status == code, (case, e.value)
