@@ -80,14 +80,16 @@ int main() {
   (void)spinsum_batch_static(&pr, 1, SPINSUM_F64, nullptr);
   // packed antisymmetric storage: invalid arguments, and valid ones with no device
   {
-    int64_t pext[6] = {2, 2, 2, 5, 5, 5}, pldb[6] = {1, 2, 4, 8, 40, 200}, pldp[4] = {1, 2, 4, 8};
+    // arrays sized for d = 4 (2d extents and strides, d + 1 packed strides)
+    int64_t pext[8] = {2, 2, 2, 5, 5, 5, 5, 5}, pldb[8] = {1, 2, 4, 8, 40, 200, 1000, 5000};
+    int64_t pldp[5] = {1, 2, 4, 8, 8};
     double Pk[1024] = {0}, Bk[2048] = {0};
     for (int d = 1; d <= 5; d++) {
       (void)spinsum_unpack(d, SPINSUM_F64, pext, Pk, pldp, Bk, pldb, nullptr);
       (void)spinsum_pack(d, SPINSUM_F32, pext, Bk, pldb, Pk, pldp, nullptr);
     }
     if (spinsum_unpack(3, SPINSUM_F64, pext, Pk, pldp, Pk + 4, pldb, nullptr) == SPINSUM_OK) bad = 1;
-    int64_t short_ldp[4] = {1, 2, 4, 7};
+    int64_t short_ldp[5] = {1, 2, 4, 7, 7};
     if (spinsum_pack(3, SPINSUM_F64, pext, Bk, pldb, Pk, short_ldp, nullptr) == SPINSUM_OK) bad = 1;
   }
   if (spinsum_last_error() == nullptr || spinsum_version() == nullptr) bad = 1;
