@@ -7,8 +7,8 @@
  *   B = alpha * sum_{sigma in S_d} a_sigma * pi_sigma(A) + beta * B
  *
  * over one group of d permuted indices of a tensor that also carries d
- * spectator indices (CCSDT: d = 3, A[a,b,c,i,j,k]; CCSDTQ: d = 4,
- * A[a,b,c,d,i,j,k,l]). pi_phi acts on the permuted group as in Def. 1-2
+ * spectator indices (CCSD: d = 2, A[a,b,i,j]; CCSDT: d = 3, A[a,b,c,i,j,k];
+ * CCSDTQ: d = 4, A[a,b,c,d,i,j,k,l]). pi_phi acts on the permuted group as in Def. 1-2
  * (Eq. 1-3): pi_phi(A)[s, i_1..i_d] = A[s, i_phi(1), ..., i_phi(d)].
  *
  * Coefficients. `coef` holds `nfactors` rows of d! doubles each; the columns
