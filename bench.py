@@ -205,6 +205,31 @@ def cpu_baseline(seconds: float = 10.0):
             "sample": f"A[16,16,16,16,16,16] ({n} doubles), same operator/mode, {reps} runs in {dt:.1f} s"}
 
 
+def paper_cpu_algorithm(reps: int = 2):
+    """The paper's own blocked CPU algorithm (Algorithms 5a/5b and 6, native
+    host library) on the host cores, on the paper-layout tensors of the tiled
+    GPU lines: best of `reps` runs each."""
+    import cpu_alg6
+    import workloads as wl
+    out = []
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    for d, n_, row in ((3, 544, 1), (4, 112, 5)):
+        shp = (n_,) * d
+        A = np.asfortranarray(wl.uniform(3, shp))
+        B = np.empty(shp, order="F")
+        coef = wl.table2(row)
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            cpu_alg6.spinsum_alg6(A, coef, factorized=True, out=B, threads=threads)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out.append({"case": f"paper layout {d}d N={n_} row{row} factorized out-of-place, paper's Alg. 6 on host",
+                    "GB/s": round(2 * A.size * 8 / best / 1e9, 2), "ms": round(best * 1e3, 2), "threads": threads})
+        del A, B
+    return out
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -545,8 +570,11 @@ def run_ours(args):
         ss.spinsum_check_status(stream.cuda_stream)
 
     cpu = None
+    host_alg = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
+        if not args.no_extra:
+            host_alg = paper_cpu_algorithm()
 
     if rank == 0:
         out = {
@@ -570,6 +598,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "paper_cpu_algorithm": host_alg,
             "paper_context": "Alg. 6 speedups over NCC 2.4-5.5x on 2x Xeon E5-2680 v3 (FP64); no absolute numbers",
             "cases": extra,
         }

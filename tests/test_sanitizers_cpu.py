@@ -1,9 +1,11 @@
-"""The oracle (C) and the host planner (C++) built with AddressSanitizer and
-UndefinedBehaviorSanitizer and run on the CPU (no GPU, no compute-sanitizer):
-every access and integer operation of the oracle's entry points on small
-inputs, and of the planner on many chain shapes, modes and layouts, plus the
-public entry points on invalid arguments and without a device (the device
-launchers are stand-ins that report "no device")."""
+"""The oracle (C), the host planner (C++) and the host blocked algorithm
+(cpu_alg6, C++) built with AddressSanitizer and UndefinedBehaviorSanitizer and
+run on the CPU (no GPU, no compute-sanitizer): every access and integer
+operation of the oracle's entry points on small inputs, of the planner on
+many chain shapes, modes and layouts, plus the public entry points on invalid
+arguments and without a device (the device launchers are stand-ins that
+report "no device"), and of the blocked algorithm on cut tiles, chains, in
+place and several threads."""
 import os
 import shutil
 import subprocess
@@ -62,4 +64,16 @@ def test_host_planner_under_asan_ubsan(tmp_path, gcc):
     if r.returncode != 0 and "sanitize" in r.stderr:
         pytest.skip("sanitizer runtime not available: " + r.stderr[-300:])
     assert r.returncode == 0, r.stderr[-4000:]
+    _run(exe)
+
+
+def test_host_alg6_under_asan_ubsan(tmp_path, gcc):
+    exe = str(tmp_path / "alg6_san")
+    cmd = ["g++", *SAN, "-ffp-contract=off", "-std=c++17", "-I", os.path.join(ROOT, "cpu_alg6"),
+           os.path.join(ROOT, "cpu_alg6", "alg6.cpp"),
+           os.path.join(ROOT, "tests", "sanitize", "alg6_driver.cpp"), "-o", exe, "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and "sanitize" in r.stderr:
+        pytest.skip("sanitizer runtime not available: " + r.stderr[-300:])
+    assert r.returncode == 0, r.stderr
     _run(exe)
