@@ -36,6 +36,16 @@
  * for the calling thread's last failure. Device-side failures (a bounded wait
  * that ran out, an element outside the fast path's range that could not be
  * handled) set a device status word that spinsum_check_status() reads.
+ *
+ * Threads. The error message and the launch count are per thread. Calls on
+ * device tensors (spinsum_2d/3d/4d, spinsum_unpack/pack) and
+ * spinsum_plan_execute on distinct plans may run concurrently from several
+ * threads. Three things are shared per process and must not be used from two
+ * threads at once: the staging pipeline of the host-tensor calls
+ * (spinsum_*_host, one per device), the parameter array of
+ * spinsum_batch_static (one per device), and the autotuning cache that every
+ * spinsum_plan_create reads (and extends when it tunes), so plans are created
+ * from one thread at a time.
  */
 #ifndef SPINSUM_H
 #define SPINSUM_H
