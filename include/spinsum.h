@@ -191,7 +191,10 @@ int spinsum_pack(int d, int dtype, const int64_t ext[], const void* B, const int
 
 /*
  * Batched plans: many independent spin summations (uneven extents, mixed d,
- * mixed coefficient sets) run by one persistent kernel launch.
+ * mixed coefficient sets) run by one persistent kernel launch. The plan's work
+ * list is the GPU form of the task-based scheduling of Sec. 4.5 (Algorithm
+ * 5a): every (problem, block of orbits) pair is a task, and the persistent
+ * CTAs take tasks in a fixed order instead of from a dynamic queue.
  *
  * spinsum_problem describes one summation exactly as the arguments of
  * spinsum_2d / spinsum_3d / spinsum_4d do (d = 2 uses the first 4 entries of
@@ -245,16 +248,23 @@ const char* spinsum_plan_describe(const spinsum_plan* plan);
  *
  * problems, nproblems, dtype: as for spinsum_plan_create; at most
  *   SPINSUM_STATIC_MAX_PROBLEMS problems, else SPINSUM_ERR_ARG.
- * The call copies the parameters into the array with cudaMemcpyAsync on
- * `stream`, then launches there; it calls no allocating routine. The first
- * call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * All calls share the one array and overwrite what they use: calls whose work
- * can overlap on the GPU (for example on two streams at once) race on it, and
- * the caller must order them.
+ * The call copies the parameters of the problems it is given (not the whole
+ * array) into the array with cudaMemcpyAsync on `stream`, then launches
+ * there; it calls no allocating routine. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture. The copy reads a host buffer that lives only
+ * for the duration of the call, so the call returns SPINSUM_ERR_ARG on a
+ * stream that is being captured. All calls share the one array and overwrite
+ * what they use: calls whose work can overlap on the GPU (for example on two
+ * streams at once) race on it, and the caller must order them.
  */
 #define SPINSUM_STATIC_MAX_PROBLEMS 64
 int spinsum_batch_static(const spinsum_problem* problems, int nproblems, int dtype, spinsum_stream_t stream);
+
+/*
+ * Error reporting and bookkeeping. These four calls are API additions with no
+ * counterpart in the paper, which describes the computation only.
+ */
 
 /* Synchronizes `stream`, then reads and clears the device status word:
  * SPINSUM_OK, SPINSUM_ERR_TIMEOUT or SPINSUM_ERR_DEVICE. */

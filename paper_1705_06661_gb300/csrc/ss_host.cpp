@@ -832,12 +832,7 @@ struct ImageShape {
   size_t probs, prefix, vec, bytes;
 };
 ImageShape image_shape(int n) {
-  ImageShape sh;
-  sh.probs = 0;
-  sh.prefix = sizeof(KParams) * (size_t)n;
-  sh.vec = sh.prefix + sizeof(int64_t) * (size_t)(n + BATCH_MAX_CLASSES);
-  sh.bytes = sh.vec + sizeof(int) * (size_t)n;
-  return sh;
+  return ImageShape{batch_offset_probs(n), batch_offset_prefix(n), batch_offset_vec(n), batch_image_bytes(n)};
 }
 
 // Fill the image with the K1-capable launches in the given order, grouped by
@@ -1119,6 +1114,15 @@ extern "C" int spinsum_batch_static(const spinsum_problem* problems, int nproble
     return fail(SPINSUM_ERR_ARG, "spinsum_batch_static takes at most %d problems (got %d)",
                 SPINSUM_STATIC_MAX_PROBLEMS, nproblems);
   cudaStream_t st = (cudaStream_t)stream;
+  // the parameter upload below reads a host buffer that lives only for this
+  // call, so a capturing stream (whose graph would read it at replay) is refused
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, "querying the stream's capture status");
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(SPINSUM_ERR_ARG, "spinsum_batch_static does not run on a stream that is being captured");
+  }
   std::vector<Launch> launches;
   for (int i = 0; i < nproblems; i++) {
     const spinsum_problem& q = problems[i];
@@ -1137,22 +1141,31 @@ extern "C" int spinsum_batch_static(const spinsum_problem* problems, int nproble
   cudaError_t e = static_scratch_ptr(&dimg);
   if (e != cudaSuccess) return cuda_fail(e, "looking up the static scratch array");
   const int nmax = SPINSUM_STATIC_MAX_PROBLEMS;
-  std::vector<unsigned char> img(batch_image_bytes(nmax), 0);
-  BatchLayout lay{reinterpret_cast<KParams*>(img.data() + batch_offset_probs(nmax)),
-                  reinterpret_cast<int64_t*>(img.data() + batch_offset_prefix(nmax)),
-                  reinterpret_cast<int*>(img.data() + batch_offset_vec(nmax))};
+  const ImageShape sh = image_shape(nmax);
+  std::vector<unsigned char> img(sh.bytes, 0);
+  BatchLayout lay{reinterpret_cast<KParams*>(img.data() + sh.probs), reinterpret_cast<int64_t*>(img.data() + sh.prefix),
+                  reinterpret_cast<int*>(img.data() + sh.vec)};
   std::vector<int> order(launches.size());
   for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
   const std::vector<ClassRange> cls = fill_batch(launches, order, 0, lay, status_ptr());
   if (!cls.empty()) {
-    // every field a kernel reads is rewritten here; unused entries stay zero
-    e = cudaMemcpyAsync(dimg, img.data(), img.size(), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "uploading the batch parameters");
+    // only the entries the kernels read: the parameters and vector widths of
+    // the n problems and the class prefix segments (n + classes entries); the
+    // rest of the array keeps whatever an earlier call left there
+    const ClassRange& last = cls.back();
+    const size_t n = (size_t)(last.first + last.n), np = (size_t)(last.pfirst + last.n + 1);
+    const size_t parts[3][2] = {{sh.probs, n * sizeof(KParams)}, {sh.prefix, np * sizeof(int64_t)},
+                                {sh.vec, n * sizeof(int)}};
+    for (const auto& pt : parts) {
+      e = cudaMemcpyAsync(static_cast<unsigned char*>(dimg) + pt[0], img.data() + pt[0], pt[1],
+                          cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "uploading the batch parameters");
+    }
   }
   const unsigned char* base = static_cast<const unsigned char*>(dimg);
-  const KParams* probs = reinterpret_cast<const KParams*>(base + batch_offset_probs(nmax));
-  const int64_t* prefix = reinterpret_cast<const int64_t*>(base + batch_offset_prefix(nmax));
-  const int* vec = reinterpret_cast<const int*>(base + batch_offset_vec(nmax));
+  const KParams* probs = reinterpret_cast<const KParams*>(base + sh.probs);
+  const int64_t* prefix = reinterpret_cast<const int64_t*>(base + sh.prefix);
+  const int* vec = reinterpret_cast<const int*>(base + sh.vec);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -275,8 +275,10 @@ struct Launch {
   bool empty = false;
 };
 
-// byte layout of a batch image for at most n problems: KParams[n], then the
-// prefix segments (n + BATCH_MAX_CLASSES int64), then the vector widths (n int)
+// byte layout of a batch image (plan memory, or the library's fixed array)
+// for at most n problems: KParams[n], then the K1-block prefix segments of the
+// (d, arithmetic) classes (class c has n_c + 1 entries, so n +
+// BATCH_MAX_CLASSES int64 in all), then the vector widths (n int)
 constexpr size_t batch_offset_probs(int n) { return (void)n, 0; }
 constexpr size_t batch_offset_prefix(int n) { return sizeof(KParams) * (size_t)n; }
 constexpr int BATCH_MAX_CLASSES = 12;  // (d, arithmetic) classes: 3 x 3, with room
@@ -284,16 +286,5 @@ constexpr size_t batch_offset_vec(int n) {
   return batch_offset_prefix(n) + sizeof(int64_t) * (size_t)(n + BATCH_MAX_CLASSES);
 }
 constexpr size_t batch_image_bytes(int n) { return batch_offset_vec(n) + sizeof(int) * (size_t)n; }
-
-// device image of a batch (plan memory, or the library's fixed array): the
-// parameters, K1-block prefix sums and vector widths of its problems, grouped
-// by (d, arithmetic) class; class c uses probs[first_c ..] and the prefix
-// segment starting at prefix[pfirst_c] (n_c + 1 entries)
-template <int NMAX>
-struct BatchImage {
-  KParams probs[NMAX];
-  int64_t prefix[NMAX + 8];
-  int vec[NMAX];
-};
 
 }  // namespace ss

@@ -28,6 +28,7 @@
 // Partial tiles at the upper edge (N not a multiple of BL) are handled by
 // bounds checks: an element orbit lies entirely inside or outside the tensor.
 #pragma once
+#include "ss_devcache.h"
 #include "ss_kernels.cuh"
 
 namespace ss {
@@ -541,29 +542,31 @@ cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
   constexpr int RUN = D == 2 ? SS_K2_RUN2 : (D == 3 ? SS_K2_RUN3 : SS_K2_RUN4);
   constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
   auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
-  constexpr int MAXDEV = 64;
-  static int ctas[MAXDEV] = {0};  // resident CTAs per device (persistent grid)
+  // resident CTAs per device (persistent grid), set up once per device
+  static DeviceCache cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
-  if (ctas[dev] == 0) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  long long ctas = 0;
+  const int rc = cache.get(dev, &ctas, [&](long long* val) {
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
     // all of the unified L1/shared array as shared memory: occupancy is set by the tiles
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (err != cudaSuccess) return (int)err;
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    ctas[dev] = per_sm * sms;
-  }
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+    if (err != cudaSuccess) return (int)err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return (int)err;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    *val = (long long)per_sm * sms;
+    return 0;
+  });
+  if (rc != 0) return rc < 0 ? cudaErrorInvalidDevice : (cudaError_t)rc;
   const int64_t ids = kp.pre[npatterns(D)];
   if (ids == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)(RUN > 0 ? (ids + RUN - 1) / RUN : (ids > ctas[dev] ? ctas[dev] : ids));
+  const unsigned grid = (unsigned)(RUN > 0 ? (ids + RUN - 1) / RUN : (ids > ctas ? ctas : ids));
   fn<<<grid, 256, smem, st>>>(kp);
   return cudaGetLastError();
 }

@@ -10,27 +10,29 @@
 #include <cuda_runtime.h>
 
 #include "../../include/spinsum.h"
+#include "ss_devcache.h"
 #include "ss_internal.h"
 
 namespace ss {
 
 static __device__ __align__(256) unsigned char g_static_scratch[batch_image_bytes(SPINSUM_STATIC_MAX_PROBLEMS)];
 
-// device address of the array on the current device, looked up once per device
+// device address of the array on the current device, looked up once per
+// device (several host threads may ask at once)
 cudaError_t static_scratch_ptr(void** out) {
-  constexpr int MAXDEV = 64;
-  static void* ptr[MAXDEV] = {nullptr};
+  static DeviceCache cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
-  if (!ptr[dev]) {
+  long long v = 0;
+  const int rc = cache.get(dev, &v, [](long long* val) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    ptr[dev] = p;
-  }
-  *out = ptr[dev];
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_static_scratch);
+    *val = (long long)(uintptr_t)p;
+    return (int)err;
+  });
+  if (rc != 0) return rc < 0 ? cudaErrorInvalidDevice : (cudaError_t)rc;
+  *out = (void*)(uintptr_t)v;
   return cudaSuccess;
 }
 

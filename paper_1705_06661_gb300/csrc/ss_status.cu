@@ -3,6 +3,7 @@
 // translation units.
 #include <cuda_runtime.h>
 
+#include "ss_devcache.h"
 #include "ss_internal.h"
 
 namespace ss {
@@ -54,17 +55,20 @@ int k1t_chunk(int d, int ar) {
   return SS_K1T3_NCW * 32 * (ar == AR_EXACT ? 2 : 4);
 }
 
-// device address of the status word, per device
+// device address of the status word, per device (looked up once per device;
+// several host threads may ask at once)
 int* status_ptr() {
-  static int* ptr[64] = {nullptr};
+  static DeviceCache cache;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!ptr[dev]) {
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  long long v = 0;
+  const int rc = cache.get(dev, &v, [](long long* val) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-    ptr[dev] = static_cast<int*>(p);
-  }
-  return ptr[dev];
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_status);
+    *val = (long long)(uintptr_t)p;
+    return (int)err;
+  });
+  return rc == 0 ? reinterpret_cast<int*>((uintptr_t)v) : nullptr;
 }
 
 // tiled kernel for the paper's N^d layout

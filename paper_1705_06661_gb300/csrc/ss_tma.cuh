@@ -17,6 +17,7 @@
 // records SPINSUM_ERR_TIMEOUT in the status word, waits (bounded again) for
 // its own copies in flight, and returns; nothing traps or hangs.
 #pragma once
+#include "ss_devcache.h"
 #include "ss_kernels.cuh"
 
 namespace ss {
@@ -248,23 +249,26 @@ template <int D, int AR, int VEC, typename T, int NCW, int NST>
 cudaError_t launch_k1t_impl(const KParams& kp, cudaStream_t st) {
   using C = K1TConfig<D, AR, VEC, T, NCW, NST>;
   auto fn = k1t_kernel<D, AR, VEC, T, NCW, NST>;
-  constexpr int MAXDEV = 64;
-  static int blocks_per_sm[MAXDEV] = {0}, sms[MAXDEV] = {0};
+  // resident CTAs per device (persistent grid), set up once per device
+  static DeviceCache cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
-  if (blocks_per_sm[dev] <= 0) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
-    blocks_per_sm[dev] = nb > 0 ? nb : 1;
-  }
+  long long ctas = 0;
+  const int rc = cache.get(dev, &ctas, [&](long long* val) {
+    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (err != cudaSuccess) return (int)err;
+    int sms = 0, nb = 0;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return (int)err;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, C::THREADS, C::SMEM);
+    if (err != cudaSuccess) return (int)err;
+    *val = (long long)sms * (nb > 0 ? nb : 1);
+    return 0;
+  });
+  if (rc != 0) return rc < 0 ? cudaErrorInvalidDevice : (cudaError_t)rc;
   const int64_t ntiles = kp.pre[npatterns(D)];
-  int64_t g = (int64_t)sms[dev] * blocks_per_sm[dev];
+  int64_t g = ctas;
   if (ntiles < g) g = ntiles;
   if (g < 1) g = 1;
   fn<<<(unsigned)g, C::THREADS, C::SMEM, st>>>(kp);

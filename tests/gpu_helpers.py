@@ -25,7 +25,7 @@ def fp64_tol(d, coef, factorized, A, alpha=1.0):
 
 
 def gpu_run(A_np, d, coef, *, factorized=False, strict=False, adjoint=False, alpha=1.0, beta=0.0, inplace=False,
-            B0=None, dtype="f64", layout="colmajor", offset=0):
+            B0=None, dtype="f64", layout="colmajor", offset=0, tma=False):
     """Copy A (numpy, any strides) to the GPU in the requested layout, run the
     spin summation through the C-ABI, return the result as numpy float64."""
     import torch
@@ -60,7 +60,7 @@ def gpu_run(A_np, d, coef, *, factorized=False, strict=False, adjoint=False, alp
     else:
         out = m.colmajor_like(A) if layout != "rowmajor" else torch.empty_like(A)
     m.spinsum(A, coef, d=d, out=None if inplace else out, factorized=factorized, strict=strict, adjoint=adjoint,
-              alpha=alpha, beta=beta, inplace=inplace)
+              alpha=alpha, beta=beta, inplace=inplace, tma=tma)
     m.spinsum_check_status(torch.cuda.current_stream().cuda_stream)
     return out.cpu().numpy().astype(np.float64)
 

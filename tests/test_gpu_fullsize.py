@@ -4,8 +4,9 @@ OpenMP over the host cores).
 
 - 3D, A[48,48,48,16,16,16] (453M doubles): Table II row 1 factorized, out of
   place (the benchmark step) and in place; an integer-valued copy bit-exact.
-- 4D, A[12]^8 (430M doubles): Table II row 6 factorized and a random 24-term
-  set expanded.
+- 4D, A[12]^8 (430M doubles): Table II rows 5 and 6 factorized and a random
+  24-term set expanded, out of place and in place; an integer-valued copy in
+  place bit-exact.
 - 64 uneven 3D blocks (V in [16,40], O in [6,14]) in one batched plan, FP64
   and FP32 storage; per-block errors against the FP64 oracle.
 - 4D, A[10]^8 through autograd: forward and backward against the oracle and
@@ -57,16 +58,33 @@ def test_config2_3d_full():
 
 
 def test_config3_4d_full():
+    """A[12]^8 in the benchmark's launch configuration: Table II row 5
+    factorized (the benchmark's operator), row 6 factorized and the random
+    24-term set expanded, each out of place and in place over the whole
+    output; an integer-valued copy in place, bit-exact, for row 5 and the
+    random set."""
     import oracle
     import paper_1705_06661_gb300 as ss
     shape = (12,) * 8
     A_np = wl.uniform(2, shape)
     A = _dev(A_np)
     B = ss.colmajor_like(A)
-    for coef, fac in ((wl.table2(6), True), (wl.random_coef(4, 103), False)):
+    sets = ((wl.table2(5), True), (wl.table2(6), True), (wl.random_coef(4, 103), False))
+    for k, (coef, fac) in enumerate(sets):
         want = oracle.spinsum(A_np, 4, coef, factorized=fac)
         ss.spinsum(A, coef, d=4, out=B, factorized=fac)
-        assert_within(_host(B), want, fp64_tol(4, coef, fac, A_np), "config 3")
+        assert_within(_host(B), want, fp64_tol(4, coef, fac, A_np), f"config 3 set {k} out of place")
+        B.copy_(A)
+        ss.spinsum(B, coef, d=4, inplace=True, factorized=fac)
+        assert_within(_host(B), want, fp64_tol(4, coef, fac, A_np), f"config 3 set {k} in place")
+        del want
+    del A
+    Ai_np = wl.integers(2, shape)
+    Ai = _dev(Ai_np)
+    for k, (coef, fac) in enumerate((sets[0], sets[2])):
+        B.copy_(Ai)
+        ss.spinsum(B, coef, d=4, inplace=True, factorized=fac)
+        assert_bitexact(_host(B), oracle.spinsum(Ai_np, 4, coef, factorized=fac), f"config 3 integer set {k} in place")
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])

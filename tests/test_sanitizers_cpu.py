@@ -77,3 +77,29 @@ def test_host_alg6_under_asan_ubsan(tmp_path, gcc):
         pytest.skip("sanitizer runtime not available: " + r.stderr[-300:])
     assert r.returncode == 0, r.stderr
     _run(exe)
+
+
+def test_threads_under_tsan(tmp_path, gcc):
+    """The per-device lookup cache of the library and the host planner with
+    its public entry points, called from many threads at once under
+    ThreadSanitizer (device launchers stubbed)."""
+    cuda = _cuda_home()
+    inc = os.path.join(cuda, "include")
+    libdir = next((p for p in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib")) if os.path.isdir(p)), None)
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")) or libdir is None:
+        pytest.skip("CUDA runtime headers or library not found")
+    exe = str(tmp_path / "thread_san")
+    csrc = os.path.join(ROOT, "paper_1705_06661_gb300", "csrc")
+    cmd = ["g++", "-fsanitize=thread", "-g", "-O1", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", inc,
+           os.path.join(csrc, "ss_host.cpp"),
+           os.path.join(ROOT, "tests", "sanitize", "host_stubs.cpp"),
+           os.path.join(ROOT, "tests", "sanitize", "thread_driver.cpp"),
+           "-o", exe, "-L", libdir, "-lcudart", f"-Wl,-rpath,{libdir}", "-lpthread", "-ldl"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and "sanitize" in r.stderr:
+        pytest.skip("sanitizer runtime not available: " + r.stderr[-300:])
+    assert r.returncode == 0, r.stderr[-4000:]
+    env = dict(os.environ, TSAN_OPTIONS="halt_on_error=1:second_deadlock_stack=1")
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-4000:]
+    assert "WARNING: ThreadSanitizer" not in r.stderr, r.stderr[-4000:]
