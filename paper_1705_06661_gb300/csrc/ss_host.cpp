@@ -194,6 +194,34 @@ void fill_mp(const std::vector<long long>& a, int* mp) {
   }
 }
 
+// the transformed orbit operators of the Klein four-group transform (d = 4):
+// weight (i, q) = sum over sigma with jmap[i][sigma] = col[i][q] of
+// smap[i][sigma] * a_sigma
+const std::array<Wht4, 8>& host_wht4() {
+  static const std::array<Wht4, 8> t = [] {
+    std::array<Wht4, 8> a{};
+    for (int p = 0; p < 8; p++) a[p] = make_wht4(p);
+    return a;
+  }();
+  return t;
+}
+
+void fill_wh(const std::vector<long long>& a, int* wh) {
+  int off = 0;
+  for (int P = 0; P < 8; P++) {
+    const Wht4& w = host_wht4()[P];
+    if (!w.ok) continue;
+    for (int i = 0; i < w.m; i++)
+      for (int q = 0; q < w.nnz[i]; q++) {
+        long long v = 0;
+        for (int s = 0; s < 24; s++)
+          if (w.jmap[i][s] == w.col[i][q]) v += w.smap[i][s] * a[s];
+        wh[off + w.woff[i] + q] = (int)v;
+      }
+    off += w.woff[w.m];
+  }
+}
+
 // polls of a bounded device-side wait before it reports SPINSUM_ERR_TIMEOUT;
 // SPINSUM_WAIT_LIMIT overrides the default (2^22 polls, well under a minute)
 long long wait_limit() {
@@ -367,6 +395,23 @@ int plan_one(const Request& r, Launch* L) {
           }
           ex = P;
         }
+        // d = 4: the Klein four-group transform (Wht4) needs the transformed
+        // low limbs (25 bits, non-negative) and high limbs (the 50-bit
+        // transformed values shifted down by 25) times the coefficient 1-norm
+        // to stay below 2^31, i.e. sum|a| <= 63 on a 48-bit grid; the other
+        // patterns then use the same grid (W = 24)
+        bool wht = false;
+        if (d == 4 && apow2) {
+          long long lx = 0;
+          for (long long v : ex) lx += v < 0 ? -v : v;
+          if (lx <= 63) {
+            wht = true;
+            W = 24;
+            kdrop = 0;
+            const double ymax = Lnorm * (std::ldexp(1.0, 2 * W) + std::ldexp(1.0, W));
+            while (ymax / std::ldexp(1.0, kdrop) + 1.0 >= std::ldexp(1.0, 50)) kdrop++;
+          }
+        }
         const bool neg = apow2 && r.alpha < 0;
         int aexp = -escale + (apow2 ? a : 0);
         const int cshift = 53 - 2 * W + kdrop + aexp;
@@ -400,6 +445,10 @@ int plan_one(const Request& r, Launch* L) {
           if (d == 2) fill_mp<2>(ex, kp.mp);
           else if (d == 3) fill_mp<3>(ex, kp.mp);
           else fill_mp<4>(ex, kp.mp);
+          if (wht) {
+            kp.flags |= KF_WHT;
+            fill_wh(ex, kp.wh);
+          }
         }
       }
     }
@@ -1229,5 +1278,48 @@ extern "C" int ss_debug_plan(int d, int O, int V, const double* coef, int nfacto
   for (int st = 0; st < MAXSTAGE; st++)
     for (int x = 0; x < 24; x++) ci[st * 24 + x] = kp.ci[st][x];
   for (int k = 0; k < MP_MAX; k++) mp[k] = kp.mp[k];
+  return SPINSUM_OK;
+}
+
+// Planner introspection for host-side tests (not part of the public ABI): the
+// Klein four-group tables of 4D pattern P as
+// [ok, m, nb, orb[6][4], nnz[24], col[24][6], woff[25]] (223 ints), and, for a
+// planned d = 4 problem (as ss_debug_plan), [flags, W, kdrop] and the wh
+// weights (WH_TOTAL ints).
+extern "C" int ss_debug_wht_tables(int P, int* out) {
+  if (P < 0 || P >= 8) return SPINSUM_ERR_ARG;
+  const Wht4& w = host_wht4()[P];
+  int k = 0;
+  out[k++] = w.ok;
+  out[k++] = w.m;
+  out[k++] = w.nb;
+  for (int o = 0; o < 6; o++)
+    for (int vi = 0; vi < 4; vi++) out[k++] = w.orb[o][vi];
+  for (int i = 0; i < 24; i++) out[k++] = w.nnz[i];
+  for (int i = 0; i < 24; i++)
+    for (int q = 0; q < 6; q++) out[k++] = w.col[i][q];
+  for (int i = 0; i < 25; i++) out[k++] = w.woff[i];
+  return SPINSUM_OK;
+}
+
+extern "C" int ss_debug_plan_wh(int O, int V, const double* coef, int nfactors, int mode, double alpha, double beta,
+                                int64_t* info, int* wh) {
+  int64_t ext[8], ld[8];
+  int64_t s = 1;
+  for (int k = 0; k < 8; k++) {
+    ext[k] = k < 4 ? V : O;
+    ld[k] = s;
+    s *= ext[k];
+  }
+  Request r{4, SPINSUM_F64, ext, (const void*)0x100000, ld, (void*)(0x100000 + 8 * s + 4096), ld,
+            coef, nfactors, mode, alpha, beta, 0};
+  Launch L;
+  int rc = plan_one(r, &L);
+  if (rc != SPINSUM_OK) return rc;
+  info[0] = L.kp.flags;
+  info[1] = L.kp.W;
+  info[2] = L.kp.kdrop;
+  info[3] = L.ar;
+  for (int k = 0; k < WH_TOTAL; k++) wh[k] = L.kp.wh[k];
   return SPINSUM_OK;
 }

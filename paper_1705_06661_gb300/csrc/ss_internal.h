@@ -16,6 +16,7 @@
 // idx[u][sigma], the member equal to t_u o sigma (Def. 2), for every sigma in
 // lexicographic order. These tables are computed at compile time.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
 namespace ss {
@@ -117,6 +118,97 @@ struct PT {
   static constexpr Pattern<D> t = make_pattern<D>(P);
 };
 
+// ---------------------------------------------------------------------------
+// Klein four-group transform of 4D orbits. V = {e, (01)(23), (02)(13),
+// (03)(12)} (0-based places) is a normal subgroup of S_4. Where no double
+// transposition fixes the orbit's canonical tuple (every pattern but
+// (0,0,1,1) and (0,0,0,0)), V acts freely on the members from the right
+// (t -> t o v), so they fall into m/4 V-orbits of 4. Transforming each
+// V-orbit with the characters of V = Z_2 x Z_2 (a 4-point Walsh-Hadamard
+// transform, entries +-1) turns every pi_sigma into a signed permutation of
+// the transformed values (pi_sigma o pi_v = pi_(sigma v sigma^-1) o pi_sigma
+// maps V-orbits to V-orbits and characters to characters), so the orbit
+// operator sum_sigma a_sigma pi_sigma becomes a sparse matrix whose entries
+// are signed sums of the a_sigma: 6 nonzeros per row for the 24-member orbit
+// (144 products instead of 576), 3 or 6 for the 12-member orbits (54 instead
+// of 144), 1 or 3 for the 4-member orbits (10 instead of 16). The inverse
+// transform is the transpose divided by 4.
+// ---------------------------------------------------------------------------
+constexpr int KLEIN[4] = {0, 7, 16, 23};  // lex indices of e, (01)(23), (02)(13), (03)(12); v_a o v_b = v_(a xor b)
+
+constexpr int chi4(int k, int vi) {  // character k of V at v_vi: (-1)^popcount(k & vi)
+  return ((k & vi & 1) ^ ((k & vi) >> 1 & 1)) ? -1 : 1;
+}
+
+struct Wht4 {
+  bool ok = false;        // V acts freely on the members
+  int m = 0, nb = 0;      // members, V-orbits (m = 4 nb)
+  int orb[6][4] = {};     // member of V-orbit o at v_vi: (representative) o v_vi
+  int nnz[24] = {};       // transformed row i = 4 o + k (character k of V-orbit o): nonzeros
+  int col[24][6] = {};    // their transformed columns
+  int woff[25] = {};      // row i's weights: w[woff[i] .. woff[i] + nnz[i])
+  int jmap[24][24] = {};  // pi_sigma (lex index s) sends row i to column jmap[i][s] ...
+  int smap[24][24] = {};  // ... with sign smap[i][s]; the weight of (i, j) is sum over s with
+                          // jmap[i][s] = j of smap[i][s] * a_s
+};
+
+constexpr Wht4 make_wht4(int P) {
+  Wht4 w{};
+  const Pattern<4> pt = make_pattern<4>(P);
+  w.m = pt.m;
+  int memorb[24] = {}, memvi[24] = {};
+  for (int u = 0; u < 24; u++) memorb[u] = -1;
+  for (int u = 0; u < pt.m; u++) {
+    if (memorb[u] >= 0) continue;
+    if (w.nb >= 6) return w;
+    for (int vi = 0; vi < 4; vi++) {
+      const int v = pt.idx[u][KLEIN[vi]];
+      if (memorb[v] >= 0) return w;  // a double transposition fixes a member: not free
+      memorb[v] = w.nb;
+      memvi[v] = vi;
+      w.orb[w.nb][vi] = v;
+    }
+    w.nb++;
+  }
+  for (int o = 0; o < w.nb; o++)
+    for (int k = 0; k < 4; k++) {
+      const int i = 4 * o + k;
+      for (int s = 0; s < 24; s++) {
+        // M_s[i][4 o' + k'] = 1/4 sum_vi chi_k(vi) chi_k'(vi'), where member
+        // orb[o][vi] o sigma = orb[o'][vi']
+        const int o2 = memorb[pt.idx[w.orb[o][0]][s]];
+        for (int k2 = 0; k2 < 4; k2++) {
+          int acc = 0;
+          for (int vi = 0; vi < 4; vi++) acc += chi4(k, vi) * chi4(k2, memvi[pt.idx[w.orb[o][vi]][s]]);
+          if (acc == 4 || acc == -4) {
+            w.jmap[i][s] = 4 * o2 + k2;
+            w.smap[i][s] = acc / 4;
+          }
+        }
+        bool seen = false;
+        for (int q = 0; q < w.nnz[i]; q++) seen = seen || w.col[i][q] == w.jmap[i][s];
+        if (!seen) {
+          if (w.nnz[i] >= 6) return Wht4{};
+          w.col[i][w.nnz[i]++] = w.jmap[i][s];
+        }
+      }
+      w.woff[i + 1] = w.woff[i] + w.nnz[i];
+    }
+  w.ok = true;
+  return w;
+}
+
+// offsets of each transformable pattern's weights in the wh table
+constexpr int wh_offset(int P) {
+  int o = 0;
+  for (int q = 0; q < P; q++) {
+    const Wht4 w = make_wht4(q);
+    if (w.ok) o += w.woff[w.m];
+  }
+  return o;
+}
+constexpr int WH_TOTAL = 144 + 3 * 54 + 2 * 10;
+
 // offsets of each pattern's dense expanded matrix in the M table
 template <int D>
 constexpr int mp_offset(int P) {
@@ -210,6 +302,10 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_4D_MINBLOCKS
 #define SS_4D_MINBLOCKS 3
 #endif
+// the same for the K1 kernel of d = 4 orbits through the Klein four-group transform
+#ifndef SS_4DW_MINBLOCKS
+#define SS_4DW_MINBLOCKS 3
+#endif
 
 constexpr int MAXSTAGE = 8;
 constexpr int MAXSTAGE_EXACT = 3;  // the exact core unrolls at most this many stages
@@ -222,6 +318,7 @@ enum {
   KF_BETA = 1,        // beta != 0: read B_old
   KF_ALPHA_MUL = 2,   // exact path: alpha is not a power of two, multiply at the end
   KF_KDROP = 4,       // exact path: round the fixed-point sum before conversion
+  KF_WHT = 8,         // exact path, d = 4: freely transformable orbits through the Klein four-group transform
 };
 
 // Kernel parameters (passed by value as a __grid_constant__, or from a
@@ -250,6 +347,7 @@ struct alignas(16) KParams {
   unsigned emin, emax;          // fast path when the max exponent field lies in [emin, emax]
   int ci[MAXSTAGE][24];         // sigma-list coefficients per stage, scaled integers (application order)
   int mp[MP_MAX];               // degenerate patterns: expanded orbit matrices M_p, scaled integers
+  int wh[WH_TOTAL];             // d = 4 with KF_WHT: transformed orbit operators (Wht4), scaled integers
   double cd[MAXSTAGE][24];      // sigma-list coefficients per stage (strict path, application order)
   float cf[MAXSTAGE][24];       // the same rounded to FP32 (FP32 path)
   float alphaf, betaf;

@@ -41,6 +41,12 @@ struct Pat {
   __device__ __forceinline__ static int idx(int u, int s) { return kPattern<D, P>.idx[u][s]; }
 };
 
+// Klein four-group tables of the 4D patterns (see Wht4)
+template <int P>
+__device__ constexpr Wht4 kWht = make_wht4(P);
+template <int P>
+constexpr bool wht_ok() { return make_wht4(P).ok; }
+
 // C(n, k) for k <= 4 with constant divisors (no 64-bit division routine);
 // k is a compile-time constant at every call site after unrolling
 __device__ __forceinline__ int64_t binom(int64_t n, int k) {
@@ -254,6 +260,89 @@ __device__ __forceinline__ bool exact_core_grouped4(const KParams& kp, const dou
   return true;
 }
 
+// The exact fixed-point core of a freely transformable d = 4 orbit through
+// the Klein four-group transform (Wht4). Each input becomes one signed
+// integer X on the 48-bit grid (kp.s0 = 5) of the largest input, exactly as
+// the two limbs of exact_limbs join; every V-orbit's four X go through the
+// 4-point Walsh-Hadamard transform (64-bit, below 2^50), whose results are
+// split into a non-negative 25-bit low limb and a high limb; the sparse
+// transformed operator (kp.wh) runs on int32 IMAD per limb (the planner
+// keeps sum|a| <= 63, so both limb sums stay below 2^31); the two limb sums
+// are joined in 64 bits and the inverse transform (the same butterflies)
+// gives 4 Y, Y the integer sum sum_v M[u][v] X_v of the dense core. Rounding
+// off kdrop + 2 bits of 4 Y is rounding off kdrop bits of Y, so outputs are
+// bit-identical to exact_core on the same grid. Outputs go to sink(u, y).
+template <int P, class Sink>
+__device__ __forceinline__ bool exact_core_wht4(const KParams& kp, const double (&x)[Pat<4, P>::M], Sink&& sink) {
+  constexpr int M = Pat<4, P>::M, NB = M / 4;
+  constexpr int WOFF = wh_offset(P);
+  unsigned E = 0;
+#pragma unroll
+  for (int v = 0; v < M; v++) E = max(E, (unsigned)__double2hiint(x[v]) & 0x7FF00000u);
+  if (E < kp.emin || E > kp.emax) {
+    unsigned any = 0;
+    if (E == 0) {
+#pragma unroll
+      for (int v = 0; v < M; v++) any |= ((unsigned)__double2hiint(x[v]) & 0x7FFFFFFFu) | (unsigned)__double2loint(x[v]);
+    }
+    if (E != 0 || any != 0) return false;
+    E = kp.emin;
+  }
+  int l0[M], l1[M];  // transformed values (row 4 o + k), low 25 bits and the rest
+#pragma unroll
+  for (int o = 0; o < NB; o++) {
+    long long X[4];
+#pragma unroll
+    for (int vi = 0; vi < 4; vi++) {
+      const double xv = x[kWht<P>.orb[o][vi]];
+      const unsigned hi = (unsigned)__double2hiint(xv), lo = (unsigned)__double2loint(xv);
+      const unsigned k = ((E - (hi & 0x7FF00000u)) >> 20) + (unsigned)kp.s0;
+      const unsigned long long mant = ((unsigned long long)((hi & 0x000FFFFFu) | 0x00100000u) << 32) | lo;
+      const long long q = (long long)shr64(mant, k);
+      const long long sg = (long long)((int)hi >> 31);
+      X[vi] = (q ^ sg) - sg;
+    }
+    const long long a0 = X[0] + X[1], a1 = X[0] - X[1], a2 = X[2] + X[3], a3 = X[2] - X[3];
+    const long long xh[4] = {a0 + a2, a1 + a3, a0 - a2, a1 - a3};  // characters 0..3
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      l0[4 * o + k] = (int)((unsigned)xh[k] & 0x1FFFFFFu);
+      l1[4 * o + k] = (int)(xh[k] >> 25);
+    }
+  }
+  const unsigned chi = E + (unsigned)kp.cexp;
+  const double C = __hiloint2double((int)chi, 0);
+  const int sh = kp.kdrop + 2;
+  const long long r4 = kp.rnd << 2;
+#pragma unroll
+  for (int o = 0; o < NB; o++) {
+    long long yh[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int i = 4 * o + k;
+      int a = 0, b = 0;
+#pragma unroll
+      for (int q = 0; q < 6; q++) {
+        if (q < kWht<P>.nnz[i]) {
+          const int w = kp.wh[WOFF + kWht<P>.woff[i] + q];
+          a += w * l0[kWht<P>.col[i][q]];
+          b += w * l1[kWht<P>.col[i][q]];
+        }
+      }
+      yh[k] = ((long long)b << 25) + (long long)a;
+    }
+    const long long b0 = yh[0] + yh[1], b1 = yh[0] - yh[1], b2 = yh[2] + yh[3], b3 = yh[2] - yh[3];
+    const long long y4[4] = {b0 + b2, b1 + b3, b0 - b2, b1 - b3};  // 4 Y at v_0..v_3
+#pragma unroll
+    for (int vi = 0; vi < 4; vi++) {
+      const long long Y = (y4[vi] + r4) >> sh;
+      const double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
+      sink(kWht<P>.orb[o][vi], __dsub_rn(Dv, C));
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // one orbit element group: x (inputs, m members) -> y (outputs), incl. alpha/beta
 // ---------------------------------------------------------------------------
@@ -366,6 +455,25 @@ static __device__ __noinline__ void strict_fallback_generic4(const KParams& kp, 
   }
 }
 
+// The same for a d = 4 orbit of pattern P on the transformed path.
+template <int P>
+static __device__ __noinline__ void strict_fallback4(const KParams& kp, const int64_t* offA, const int64_t* offB,
+                                                     int64_t s) {
+  constexpr int M = Pat<4, P>::M;
+  const double* A = static_cast<const double*>(kp.A);
+  double* B = static_cast<double*>(kp.B);
+  double x[M];
+  for (int u = 0; u < M; u++) x[u] = A[offA[u] + s];
+  strict_core<4, P>(kp, x);
+  const bool beta = kp.flags & KF_BETA;
+  for (int u = 0; u < M; u++) {
+    double* dst = B + offB[u] + s;
+    double v = __dmul_rn(kp.alpha, x[u]);
+    if (beta) v = add_beta(v, *dst, kp.beta);
+    *dst = v;
+  }
+}
+
 // The generic d = 4 group when alpha is not a power of two (the fixed-point
 // path cannot fold it into the conversion): reloads its inputs and stores
 // alpha S(x) + beta B. Out of line and taken by a uniform branch before the
@@ -391,7 +499,11 @@ static __device__ __noinline__ void scaled_generic4(const KParams& kp, const int
 // offsets of A and B to shared memory; the CTA then streams cpb chunks of
 // VEC * blockDim spectator positions through registers.
 // ---------------------------------------------------------------------------
-template <int D, int P, int AR, int VEC, typename T, int NST = 0>
+//
+// XW selects the Klein four-group path of d = 4 exact orbits: 0 never, 1 for
+// every transformable pattern (the planner set KF_WHT), 2 when the problem's
+// KF_WHT flag says so (batched kernels, whose problems differ).
+template <int D, int P, int AR, int VEC, typename T, int NST = 0, int XW = 0>
 __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t c0, int64_t c1) {
   constexpr int M = Pat<D, P>::M;
   __shared__ int64_t soff[2][24];
@@ -418,6 +530,25 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
   const T* A = static_cast<const T*>(kp.A);
   T* B = static_cast<T*>(kp.B);
   const int64_t step = (int64_t)blockDim.x * VEC;
+  if constexpr (D == 4 && AR == AR_EXACT && VEC == 1 && wht_ok<P>() && XW != 0) {
+    if (XW == 1 || (kp.flags & KF_WHT)) {
+      const bool beta = kp.flags & KF_BETA;
+      for (int64_t c = c0; c < c1; c++) {
+        const int64_t s = c * step + (int64_t)threadIdx.x;
+        if (s >= kp.S) break;
+        double x[M];
+#pragma unroll
+        for (int u = 0; u < M; u++) x[u] = A[soff[0][u] + s];
+        auto sink = [&](int u, double v) {
+          T* dst = B + soff[1][u] + s;
+          if (beta) v = add_beta(v, *dst, kp.beta);
+          *dst = v;
+        };
+        if (!exact_core_wht4<P>(kp, x, sink)) strict_fallback4<P>(kp, soff[0], soff[1], s);
+      }
+      return;
+    }
+  }
   for (int64_t c = c0; c < c1; c++) {
     const int64_t s = c * step + (int64_t)threadIdx.x * VEC;
     if (s >= kp.S) break;
@@ -489,7 +620,7 @@ __device__ __forceinline__ int find_pattern(const int64_t* pre, int64_t b) {
 
 // one K1 block of work: block index b of the problem's grid -> (pattern,
 // orbit, chunk range)
-template <int D, int AR, int VEC, typename T>
+template <int D, int AR, int VEC, typename T, int XW = 0>
 __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   const int p = find_pattern<D>(kp.pre, b);
   const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;  // blocks per orbit
@@ -499,25 +630,26 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   const int64_t c0 = cb * kp.cpb;
   const int64_t c1 = min(kp.nchunk, c0 + kp.cpb);
   switch (p) {
-    case 0: k1_body<D, 0, AR, VEC, T>(kp, orb, c0, c1); break;
-    case 1: k1_body<D, 1, AR, VEC, T>(kp, orb, c0, c1); break;
-    case 2: if constexpr (npatterns(D) > 2) k1_body<D, 2, AR, VEC, T>(kp, orb, c0, c1); break;
-    case 3: if constexpr (npatterns(D) > 3) k1_body<D, 3, AR, VEC, T>(kp, orb, c0, c1); break;
+    case 0: k1_body<D, 0, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+    case 1: k1_body<D, 1, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+    case 2: if constexpr (npatterns(D) > 2) k1_body<D, 2, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+    case 3: if constexpr (npatterns(D) > 3) k1_body<D, 3, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
     default:
       if constexpr (D == 4) {
         switch (p) {
-          case 4: k1_body<D, 4, AR, VEC, T>(kp, orb, c0, c1); break;
-          case 5: k1_body<D, 5, AR, VEC, T>(kp, orb, c0, c1); break;
-          case 6: k1_body<D, 6, AR, VEC, T>(kp, orb, c0, c1); break;
-          case 7: k1_body<D, 7, AR, VEC, T>(kp, orb, c0, c1); break;
+          case 4: k1_body<D, 4, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+          case 5: k1_body<D, 5, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+          case 6: k1_body<D, 6, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+          case 7: k1_body<D, 7, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
         }
       }
   }
 }
 
-template <int D, int AR, int VEC, typename T>
-__global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? SS_4D_MINBLOCKS : 1) k1_kernel(const __grid_constant__ KParams kp) {
-  k1_block<D, AR, VEC, T>(kp, blockIdx.x);
+template <int D, int AR, int VEC, typename T, int XW = 0>
+__global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? (XW ? SS_4DW_MINBLOCKS : SS_4D_MINBLOCKS) : 1)
+    k1_kernel(const __grid_constant__ KParams kp) {
+  k1_block<D, AR, VEC, T, XW>(kp, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -536,7 +668,7 @@ __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int6
   if constexpr (VMAX >= 2) {
     if (vec == 2) { k1_block<D, AR, 2, T>(kp, b); return; }
   }
-  k1_block<D, AR, 1, T>(kp, b);
+  k1_block<D, AR, 1, T, 2>(kp, b);
 }
 
 template <int D, int AR, typename T>
