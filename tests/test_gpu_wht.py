@@ -3,9 +3,10 @@
 fixed-point core and the oracle.
 
 The transformed path computes the same integer sums on the same 48-bit grid
-as the dense core, so its results must be bit-identical to the general-stride
-kernel (which applies the dense orbit matrices) on any finite input, and
-within the FP64 tolerance of the oracle; integer-valued inputs are exact.
+as the dense core, so its results must be bit-identical to the same kernel
+with the dense orbit matrices (SPINSUM_4D_DENSE_CORE=1 selects them) on any
+input, and within the FP64 tolerance of the oracle; integer-valued inputs are
+exact.
 Covered: Table II rows 5, 6, 12, 18, 21 and random sets, expanded and
 factorized, out of place and in place (several spectator chunks per CTA),
 beta, negative power-of-two alpha, every orbit pattern (O = 1..7), a set
@@ -24,15 +25,23 @@ SETS = [("row5", wl.table2(5), True), ("row6", wl.table2(6), True), ("row12", wl
         ("random105", wl.random_coef(4, 105), False), ("dense72", np.full((1, 24), 3.0), False)]
 
 
+def _dense(monkeypatch, *a, **kw):
+    monkeypatch.setenv("SPINSUM_4D_DENSE_CORE", "1")
+    try:
+        return gpu_run(*a, **kw)
+    finally:
+        monkeypatch.delenv("SPINSUM_4D_DENSE_CORE")
+
+
 @pytest.mark.parametrize("shape", [(3, 3, 3, 3, 7, 7, 7, 7), (8, 8, 8, 8, 6, 6, 6, 6)])
-def test_transform_equals_dense_core(shape):
+def test_transform_equals_dense_core(monkeypatch, shape):
     import oracle
     A = wl.uniform(30, shape)
     for name, coef, fac in SETS:
         want = oracle.spinsum(A, 4, coef, factorized=fac)
         k1 = gpu_run(A, 4, coef, factorized=fac)
-        kg = gpu_run(A, 4, coef, factorized=fac, layout="sliced")   # general kernel, dense matrices
-        assert_bitexact(k1, kg, f"{name} transformed vs dense")
+        dense = _dense(monkeypatch, A, 4, coef, factorized=fac)
+        assert_bitexact(k1, dense, f"{name} transformed vs dense")
         assert_within(k1, want, fp64_tol(4, coef, fac, A), f"{name} vs oracle")
         ip = gpu_run(A, 4, coef, factorized=fac, inplace=True)
         assert_bitexact(ip, k1, f"{name} in place")
@@ -62,7 +71,7 @@ def test_alpha_beta_in_and_out_of_place(alpha, beta):
     assert_bitexact(gpu_run(A, 4, coef, alpha=alpha, beta=beta, inplace=True), want_ip, "in place")
 
 
-def test_out_of_range_groups_take_the_strict_core():
+def test_out_of_range_groups_take_the_strict_core(monkeypatch):
     """Zero groups stay on the fixed-point path; groups with tiny, huge or
     non-finite members take the strict core, which matches the oracle bit
     for bit."""
@@ -80,9 +89,9 @@ def test_out_of_range_groups_take_the_strict_core():
     coef = wl.table2(5)
     want = oracle.spinsum(A, 4, coef)
     got = gpu_run(A, 4, coef)
-    kg = gpu_run(A, 4, coef, layout="sliced")
+    dense = _dense(monkeypatch, A, 4, coef)
     assert np.array_equal(np.isnan(got), np.isnan(want))
     fin = np.isfinite(want)
     assert np.array_equal(got[~fin & ~np.isnan(want)], want[~fin & ~np.isnan(want)])
     assert np.abs(got[fin] - want[fin]).max() <= 1e-14 * 60 * np.abs(A[np.isfinite(A)]).max()
-    assert_bitexact(got, kg, "transformed vs dense on special values")
+    assert_bitexact(got, dense, "transformed vs dense on special values")

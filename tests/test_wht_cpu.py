@@ -159,3 +159,12 @@ def test_eligibility(lib):
     assert info["flags"] & KF_WHT
     info, _ = plan_wh(lib, wl.table2(5), mode=4)        # strict FP64
     assert info["arith"] == 1 and not info["flags"] & KF_WHT
+
+
+def test_dense_core_switch_keeps_the_grid(lib, monkeypatch):
+    monkeypatch.setenv("SPINSUM_4D_DENSE_CORE", "1")
+    info, _ = plan_wh(lib, wl.table2(5))
+    assert info["arith"] == 0 and not info["flags"] & KF_WHT and info["W"] == 24
+    monkeypatch.delenv("SPINSUM_4D_DENSE_CORE")
+    info, _ = plan_wh(lib, wl.table2(5))
+    assert info["flags"] & KF_WHT and info["W"] == 24
