@@ -57,6 +57,15 @@ def _stale(src, obj, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False, jobs: int | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    # objects built with other SPINSUM_NVCC_FLAGS are stale too
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags = os.environ.get("SPINSUM_NVCC_FLAGS", "").strip()
+    try:
+        old = open(stamp).read()
+    except OSError:
+        old = None
+    if old != flags:
+        force = True
     todo = [c for c in _commands() if force or _stale(c[0], c[1], c[3])]
     if verbose:
         print(f"[spinsum build] {len(todo)} translation unit(s) to compile")
@@ -73,6 +82,8 @@ def build(verbose: bool = False, force: bool = False, jobs: int | None = None) -
             for src in ex.map(run, todo):
                 if verbose:
                     print(f"[spinsum build] compiled {os.path.basename(src)}")
+    with open(stamp, "w") as f:
+        f.write(flags)
     objs = [c[1] for c in _commands()]
     if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lrt", "-ldl", "-lpthread"]

@@ -506,7 +506,10 @@ int plan_one(const Request& r, Launch* L) {
       kp.nchunk = (S + per - 1) / per;
       // about 8192 positions per member per block, spread evenly over the
       // blocks of an orbit (40 chunks: 20 + 20, not 32 + 8)
-      const int64_t cpb0 = std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, 8192 / per));
+      // (d = 4 through the Klein four-group transform: SS_K1_POS4, measured best
+      // with the L2 prefetch of the next chunk)
+      const int64_t pos = (d == 4 && (kp.flags & KF_WHT)) ? SS_K1_POS4 : 8192;
+      const int64_t cpb0 = std::min<int64_t>(kp.nchunk, std::max<int64_t>(1, pos / per));
       const int64_t nbo = (kp.nchunk + cpb0 - 1) / cpb0;
       kp.cpb = (int)((kp.nchunk + nbo - 1) / nbo);
       const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;

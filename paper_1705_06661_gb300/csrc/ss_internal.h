@@ -302,6 +302,15 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_4D_MINBLOCKS
 #define SS_4D_MINBLOCKS 3
 #endif
+// K1, d = 4 transform path: spectator positions per member per block
+#ifndef SS_K1_POS4
+#define SS_K1_POS4 5120
+#endif
+// K1, d = 4 transform path: bulk L2 prefetch of the member runs this many
+// chunks ahead (0: none)
+#ifndef SS_4DW_PREFETCH
+#define SS_4DW_PREFETCH 1
+#endif
 // the same for the K1 kernel of d = 4 orbits through the Klein four-group transform
 #ifndef SS_4DW_MINBLOCKS
 #define SS_4DW_MINBLOCKS 3

@@ -535,6 +535,17 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
       const bool beta = kp.flags & KF_BETA;
       for (int64_t c = c0; c < c1; c++) {
         const int64_t s = c * step + (int64_t)threadIdx.x;
+        if constexpr (SS_4DW_PREFETCH) {
+          // thread u < M asks L2 for member u's run SS_4DW_PREFETCH chunks ahead
+          const int64_t sn = (c + SS_4DW_PREFETCH) * step;
+          if (c + SS_4DW_PREFETCH < c1 && threadIdx.x < M && sn < kp.S) {
+            const int64_t n = min((int64_t)step, kp.S - sn);
+            const uintptr_t a = reinterpret_cast<uintptr_t>(A + soff[0][threadIdx.x] + sn);
+            const unsigned bytes = (unsigned)(n * (int64_t)sizeof(T)) & ~15u;
+            if ((a & 15) == 0 && bytes > 0)
+              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+          }
+        }
         if (s >= kp.S) break;
         double x[M];
 #pragma unroll

@@ -33,7 +33,7 @@ def _dense(monkeypatch, *a, **kw):
         monkeypatch.delenv("SPINSUM_4D_DENSE_CORE")
 
 
-@pytest.mark.parametrize("shape", [(3, 3, 3, 3, 7, 7, 7, 7), (8, 8, 8, 8, 6, 6, 6, 6)])
+@pytest.mark.parametrize("shape", [(3, 3, 3, 3, 7, 7, 7, 7), (8, 8, 8, 8, 6, 6, 6, 6), (6, 5, 7, 4, 5, 5, 5, 5)])
 def test_transform_equals_dense_core(monkeypatch, shape):
     import oracle
     A = wl.uniform(30, shape)
