@@ -339,6 +339,42 @@ def best_of(fn, reps, stream):
     return loop, min(ts)
 
 
+def extra_cases_contract(ss, wl, dev, stream, A, B, coef):
+    """The summation fused into a contraction over the permuted group,
+    C[s, y] = sum_t S(A)[s, t] W[y, t] on the benchmark tensor (S(A) never
+    stored), against the unfused pair (the summation into B, then the
+    contraction kernel alone on B) and, for context, cuBLAS DGEMM for the
+    contraction alone. Both kernels are bound by the FP64 pipe (Y multiply-adds
+    per element of A); the fused call saves the write and re-read of S(A)."""
+    import torch
+    out = []
+    spec = tuple(A.shape[:3])
+    S = int(np.prod(spec))
+    T = int(np.prod(A.shape[3:]))
+    n = A.numel()
+    Braw = B.permute(*reversed(range(6))).reshape(T, S)     # B's storage as a (T, S) row-major matrix
+    for Y in (4, 8, 32, 128):
+        W = ss.colmajor_empty((Y, T), device=dev)
+        W.copy_(torch.from_numpy(wl.uniform(7, (Y, T))).to(dev))
+        C = ss.colmajor_empty(spec + (Y,), device=dev)
+        reps = 5 if Y <= 32 else 2
+        fused, _ = best_of(lambda: ss.contract(A, coef, W, out=C, factorized=True), reps, stream)
+        summ, _ = best_of(lambda: ss.spinsum(A, coef, d=3, out=B, factorized=True), reps, stream)
+        plain, _ = best_of(lambda: ss.contract(B, None, W, out=C), reps, stream)
+        Wraw = W.permute(1, 0)
+        cublas, _ = best_of(lambda: torch.matmul(Wraw.t(), Braw), reps, stream)
+        tf = 2 * n * Y / fused / 1e12
+        out.append({"case": f"fused summation+contraction Y={Y} (3d row1 factorized, A[48^3,16^3] x W[{Y},16^3])",
+                    "ms": round(fused * 1e3, 3), "unfused_ms": round((summ + plain) * 1e3, 3),
+                    "unfused_parts_ms": [round(summ * 1e3, 3), round(plain * 1e3, 3)],
+                    "speedup_vs_unfused": round((summ + plain) / fused, 3),
+                    "cublas_dgemm_contraction_only_ms": round(cublas * 1e3, 3),
+                    "fp64_TFLOPs": round(tf, 3), "bound": "fp64",
+                    "frac_of_nominal_fp64": round(tf / 1.25, 3)})
+        del W, C
+    return out
+
+
 def extra_cases_batched_and_autograd(ss, wl, dev, stream, hbm_peak):
     """The batched workload (64 uneven 3D blocks, one persistent launch per
     class, replayed from a CUDA graph; FP64 and FP32 storage) and the
@@ -488,7 +524,10 @@ def run_ours(args):
         mn, one = best_of(fn, reps, stream)
         extra.append({"case": "3d row1 factorized fp32-storage", "GB/s": round(2 * N * 4 / mn / 1e9, 1),
                       "ms": round(mn * 1e3, 4), "frac": round(2 * N * 4 / mn / 1e9 / hbm_peak, 4)})
-        del A32, B32, A, B
+        del A32, B32
+        torch.cuda.empty_cache()
+        extra += extra_cases_contract(ss, wl, dev, stream, A, B, coef)
+        del A, B
         torch.cuda.empty_cache()
         shape4 = (12,) * 8
         A4 = ss.colmajor_empty(shape4, device=dev)

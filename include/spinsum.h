@@ -159,6 +159,41 @@ int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_
                     int inplace, void* workspace, size_t workspace_bytes, spinsum_stream_t stream);
 
 /*
+ * spinsum_contract -- the spin summation fused into the contraction it feeds.
+ * The spin-summed amplitudes of CC theory are intermediates of tensor
+ * contractions (Sec. 1; Sec. 6 names the kernels around the summation as the
+ * next target). This call contracts the summed tensor over its whole permuted
+ * group without storing it:
+ *
+ *   C[s, y] = sum_t S(A)[s, t] * W[y, t]      (coef != NULL)
+ *   C[s, y] = sum_t A[s, t] * W[y, t]         (coef == NULL: the contraction alone)
+ *
+ * s runs over the S = ext[0] * .. * ext[d-1] spectator positions, t over the
+ * O^d tuples of the permuted group (column-major index t = i_1 + O i_2 + ...),
+ * y over 0 .. Y-1.
+ *
+ * d      : 2, 3 or 4.
+ * ext    : 2d extents: d spectators, then d equal permuted extents O.
+ * A      : FP64 device tensor, dense column-major (spectators fastest).
+ * coef, nfactors, mode : the operator, as for spinsum_3d (EXPANDED or
+ *          FACTORIZED, optionally | ADJOINT, | STRICT); ignored when coef is
+ *          NULL. alpha = 1, beta = 0.
+ * W      : FP64 device matrix W[y + ldw * t] (y fastest), ldw >= Y.
+ * C      : FP64 device matrix C[s + ldc * y] (s fastest), ldc >= S; written,
+ *          never read; must not overlap A or W.
+ * stream : cudaStream_t to launch on.
+ *
+ * Every element of S(A) is formed in registers (the cores of spinsum_3d, so
+ * with the exact core S(A) equals what spinsum_3d/4d would store) and
+ * multiplied into FP64 accumulators in orbit order; A is read once per group
+ * of 16 columns of C. FP64 only. Errors: SPINSUM_ERR_ARG (bad d, extents,
+ * leading dimensions, pointers or mode bits), SPINSUM_ERR_ALIAS (C overlaps A
+ * or W), SPINSUM_ERR_CUDA. Asynchronous on `stream`; allocates nothing.
+ */
+int spinsum_contract(int d, const int64_t ext[], const void* A, const double* coef, int nfactors, int mode,
+                     const void* W, int64_t Y, int64_t ldw, void* C, int64_t ldc, spinsum_stream_t stream);
+
+/*
  * Packed antisymmetric storage (tensor unpacking, named in Sec. 2 and Sec. 6
  * as a further use of the orbit traversal). An antisymmetric tensor B over
  * its d permuted indices is stored as P[s, r]: one value per strictly

@@ -174,3 +174,21 @@ def pack(B: np.ndarray, d: int) -> np.ndarray:
     for t0 in itertools.combinations(range(O), d):
         P[..., colex_rank(t0)] = B[(Ellipsis,) + t0]
     return P
+
+
+def contract(A: np.ndarray, d: int, coef, W: np.ndarray, factorized: bool = False) -> np.ndarray:
+    """Contraction over the permuted index group of the spin-summed tensor:
+    C[s, y] = sum_t S(A)[s, t] * W[y, t], the use the summation feeds
+    (Sec. 1, Sec. 6); coef None contracts A itself. t is the column-major
+    index of the permuted tuple (first permuted index fastest), s that of the
+    spectator positions. W has shape (Y, O**d). Returns C with the spectator
+    axes then one axis of length Y. Written as the spin summation above
+    followed by one matrix product (numpy)."""
+    nspec = A.ndim - d
+    spec = A.shape[:nspec]
+    T = int(np.prod(A.shape[nspec:])) if d else 1
+    B = A if coef is None else spinsum(A, d, coef, factorized=factorized)
+    S = int(np.prod(spec)) if nspec else 1
+    Bm = np.asarray(B).reshape((S, T), order="F")
+    C = Bm @ np.asarray(W, dtype=np.float64).T
+    return C.reshape(tuple(spec) + (W.shape[0],), order="F")

@@ -104,6 +104,9 @@ def _load() -> ctypes.CDLL:
     lib.spinsum_unpack.restype = ctypes.c_int
     lib.spinsum_pack.argtypes = [ctypes.c_int, ctypes.c_int, _I64P, _VP, _I64P, _VP, _I64P, _VP]
     lib.spinsum_pack.restype = ctypes.c_int
+    lib.spinsum_contract.argtypes = [ctypes.c_int, _I64P, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int64,
+                                     ctypes.c_int64, _VP, ctypes.c_int64, _VP]
+    lib.spinsum_contract.restype = ctypes.c_int
     return lib
 
 
@@ -152,6 +155,17 @@ def spinsum_pack(d, dtype, ext, B, ldb, P, ldp, stream) -> int:
         raise ValueError("expected 2d extents and B strides, d + 1 P strides")
     return _check(lib.spinsum_pack(int(d), int(dtype), _i64(ext), _VP(B), _i64(ldb), _VP(P), _i64(ldp),
                                    _VP(stream)))
+
+
+def spinsum_contract(d, ext, A, coef, nfactors, mode, W, Y, ldw, C, ldc, stream) -> int:
+    """spinsum_contract of the C-ABI; A, W, C and stream are integer addresses;
+    coef None contracts A itself."""
+    if len(ext) != 2 * d:
+        raise ValueError("expected 2d extents")
+    c = None if coef is None else _coef(coef)
+    return _check(lib.spinsum_contract(int(d), _i64(ext), _VP(A), _VP(None if c is None else c.ctypes.data),
+                                       int(nfactors), int(mode), _VP(W), int(Y), int(ldw), _VP(C), int(ldc),
+                                       _VP(stream)))
 
 
 def spinsum_2d(dtype, ext, A, lda, B, ldb, coef, nfactors, mode, alpha, beta, inplace, stream) -> int:

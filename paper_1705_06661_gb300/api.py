@@ -90,6 +90,48 @@ def spinsum(A: torch.Tensor, coef, *, d: int | None = None, out: torch.Tensor | 
     return out
 
 
+def contract(A: torch.Tensor, coef, W: torch.Tensor, *, d: int | None = None, out: torch.Tensor | None = None,
+             factorized: bool = False, adjoint: bool = False, strict: bool = False,
+             stream: torch.cuda.Stream | None = None) -> torch.Tensor:
+    """C[s, y] = sum_t S(A)[s, t] * W[y, t] over the permuted group, with S(A)
+    never stored (spinsum_contract); coef None contracts A itself. A: FP64,
+    dense column-major (d spectators, d permuted indices). W: FP64, shape
+    (Y, O**d), y fastest (a column-major copy is made otherwise). Returns C of
+    shape (spectators..., Y), column-major (a new tensor unless `out` is one)."""
+    if d is None:
+        d = A.dim() // 2
+    if A.dim() != 2 * d or A.dtype != torch.float64 or not A.is_cuda:
+        raise ValueError("A must be a CUDA float64 tensor with 2d dimensions")
+    ext, lda = _dims(A, d)
+    dense = 1
+    for k in range(2 * d):
+        if ext[k] > 1 and lda[k] != dense:
+            raise ValueError("A must be dense column-major")
+        dense *= ext[k]
+    T = int(np.prod(ext[d:]))
+    if W.dim() != 2 or W.shape[1] != T or W.dtype != torch.float64 or W.device != A.device:
+        raise ValueError(f"W must be a float64 tensor of shape (Y, {T}) on A's device")
+    if W.stride(0) != 1 and W.shape[0] > 1:
+        W = colmajor_empty(W.shape, device=A.device).copy_(W)
+    Y = int(W.shape[0])
+    ldw = int(W.stride(1)) if T > 1 else max(Y, 1)
+    spec = tuple(A.shape[:d])
+    S = int(np.prod(spec))
+    if out is None:
+        out = colmajor_empty(spec + (Y,), device=A.device)
+    if tuple(out.shape) != spec + (Y,) or out.dtype != torch.float64:
+        raise ValueError("out must have shape (spectators..., Y) and dtype float64")
+    ldc = int(out.stride(-1)) if Y > 1 else max(S, 1)
+    c = None if coef is None else _coef_chain(coef, d)
+    mode = (_b.SPINSUM_FACTORIZED if factorized else _b.SPINSUM_EXPANDED) | (_b.SPINSUM_ADJOINT if adjoint else 0) \
+        | (_b.SPINSUM_STRICT if strict else 0)
+    st = (stream or torch.cuda.current_stream(A.device)).cuda_stream
+    with torch.cuda.device(A.device):
+        _b.spinsum_contract(d, ext, A.data_ptr(), c, 0 if c is None else c.shape[0], mode, W.data_ptr(), Y, ldw,
+                            out.data_ptr(), ldc, st)
+    return out
+
+
 def spinsum_host(A: torch.Tensor, coef, *, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
                  d: int | None = None, factorized: bool = False, adjoint: bool = False, strict: bool = False,
                  alpha: float = 1.0, beta: float = 0.0, inplace: bool = False,

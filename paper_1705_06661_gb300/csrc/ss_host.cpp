@@ -23,6 +23,8 @@ cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k1t(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k2(int d, const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_pack(int d, const KParams& kp, bool unpack, bool f64, int vec, cudaStream_t st);
+cudaError_t launch_kc(int d, const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
+                      int64_t ldc, cudaStream_t st);
 int k1t_chunk(int d, int ar);
 
 int* status_ptr();
@@ -620,9 +622,68 @@ int run(const Request& r, cudaStream_t st) {
   return SPINSUM_OK;
 }
 
+// The summation fused into a contraction over the permuted group:
+// C[s, y] = sum_t S(A)[s, t] W[y, t] (coef == NULL: sum_t A[s, t] W[y, t]).
+int run_contract(int d, const int64_t* ext, const void* A, const double* coef, int nfactors, int mode, const void* W,
+                 int64_t Y, int64_t ldw, void* C, int64_t ldc, cudaStream_t st) {
+  t_err.clear();
+  if (d < 2 || d > 4) return fail(SPINSUM_ERR_ARG, "d must be 2, 3 or 4");
+  if (!ext) return fail(SPINSUM_ERR_ARG, "null extent array");
+  if (Y < 0) return fail(SPINSUM_ERR_ARG, "negative Y");
+  if (mode & ~(SPINSUM_FACTORIZED | SPINSUM_ADJOINT | SPINSUM_STRICT))
+    return fail(SPINSUM_ERR_ARG, "unknown mode bits 0x%x for a contraction", mode);
+  int64_t ld[8], total = 1;
+  for (int k = 0; k < 2 * d; k++) {
+    if (ext[k] < 0) return fail(SPINSUM_ERR_ARG, "negative extent at index %d", k);
+    ld[k] = total;
+    total *= ext[k];
+  }
+  int64_t S = 1, T = 1;
+  for (int k = 0; k < d; k++) S *= ext[k];
+  for (int k = d; k < 2 * d; k++) T *= ext[k];
+  if (ldw < std::max<int64_t>(Y, 1)) return fail(SPINSUM_ERR_ARG, "ldw below Y");
+  if (ldc < std::max<int64_t>(S, 1)) return fail(SPINSUM_ERR_ARG, "ldc below the spectator block");
+  if (S == 0 || Y == 0) return SPINSUM_OK;
+  if (!C || (T > 0 && (!W || !A))) return fail(SPINSUM_ERR_ARG, "null pointer");
+  if ((uintptr_t)A % 8 || (uintptr_t)W % 8 || (uintptr_t)C % 8) return fail(SPINSUM_ERR_ARG, "misaligned pointer");
+  // C is written while A and W are read: no overlap
+  const uintptr_t c0 = (uintptr_t)C, c1 = c0 + (uintptr_t)(((Y - 1) * ldc + S) * 8);
+  const uintptr_t a0 = (uintptr_t)A, a1 = a0 + (uintptr_t)(total * 8);
+  const uintptr_t w0 = (uintptr_t)W, w1 = w0 + (uintptr_t)(T > 0 ? ((T - 1) * ldw + Y) * 8 : 0);
+  if ((T > 0 && c0 < a1 && a0 < c1) || (T > 0 && c0 < w1 && w0 < c1))
+    return fail(SPINSUM_ERR_ALIAS, "C overlaps A or W");
+  // the summation's arithmetic and orbit tables, planned as an in-place call
+  // on A (nothing is written to A)
+  const bool sum = coef != nullptr;
+  double ident[24] = {1.0};
+  Request r{d, SPINSUM_F64, ext, T > 0 ? A : C, ld, T > 0 ? const_cast<void*>(A) : C, ld, sum ? coef : ident,
+            sum ? nfactors : 1, sum ? mode : 0, 1.0, 0.0, 1};
+  Launch L;
+  if (T > 0) {
+    const int rc = plan_one(r, &L);
+    if (rc != SPINSUM_OK) return rc;
+  } else {
+    memset(&L.kp, 0, sizeof L.kp);
+    L.kp.S = S;
+    L.kp.O = (int)ext[d];
+  }
+  L.kp.S = S;
+  L.kp.status = status_ptr();
+  if ((Y + 3) / 4 > 65535) return fail(SPINSUM_ERR_UNSUPPORTED, "Y too large for one launch");
+  cudaError_t e = launch_kc(d, L.kp, L.ar, sum, static_cast<const double*>(W), Y, ldw, static_cast<double*>(C), ldc, st);
+  t_launches++;
+  if (e != cudaSuccess) return cuda_fail(e, "contraction kernel launch");
+  return SPINSUM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int spinsum_contract(int d, const int64_t ext[], const void* A, const double* coef, int nfactors, int mode,
+                     const void* W, int64_t Y, int64_t ldw, void* C, int64_t ldc, spinsum_stream_t stream) {
+  return run_contract(d, ext, A, coef, nfactors, mode, W, Y, ldw, C, ldc, (cudaStream_t)stream);
+}
 
 int spinsum_unpack(int d, int dtype, const int64_t ext[], const void* P, const int64_t ldp[], void* B,
                    const int64_t ldb[], spinsum_stream_t stream) {

@@ -166,13 +166,46 @@ __device__ __forceinline__ bool exact_limbs(const KParams& kp, const double (&x)
 // limbs (y1 * 2^W + y0) -> FP64: round off kdrop bits on the low limb
 // ((y1 2^W + y0 + r) >> k = y1 2^(W-k) + ((y0 + r) >> k) for k <= W), then one
 // subtraction of the magic constant C = chi:0
-__device__ __forceinline__ double exact_out(const KParams& kp, unsigned chi, double C, int y0, int y1) {
-  const long long Y = ((long long)y1 << kp.wk) + (long long)((y0 + (int)kp.rnd) >> kp.kdrop);
+//
+// INTCONV: build the same FP64 value with integer instructions instead (for
+// kernels whose FP64 pipe is busy with other work): the value is
+// Y * 2^(ef - 1075), ef = chi >> 20, |Y| < 2^50, so it is normalised by the
+// position of Y's leading one and packed; exact whenever the result is a
+// normal number (otherwise, which the exponent range allows only for tiny
+// alpha, the subtraction above is used).
+__device__ __forceinline__ double fixed_to_double_fp64(long long Y, unsigned chi, double C) {
   const double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
   return __dsub_rn(Dv, C);
 }
+// out of line, so that the compiler cannot predicate the subtraction into the
+// common path (a predicated-off FP64 instruction still occupies the FP64 pipe)
+static __device__ __noinline__ double fixed_to_double_fp64_call(long long Y, unsigned chi, double C) {
+  return fixed_to_double_fp64(Y, chi, C);
+}
 
-template <int D, int P, int NST = 0>
+template <bool INTCONV = false>
+__device__ __forceinline__ double fixed_to_double(long long Y, unsigned chi, double C) {
+  if constexpr (INTCONV) {
+    const unsigned long long a = Y < 0 ? 0ull - (unsigned long long)Y : (unsigned long long)Y;
+    const int p = 63 - __clzll((long long)a);
+    const int e = p + (int)(chi >> 20) - 52;
+    if (Y != 0 && e <= 0) return fixed_to_double_fp64_call(Y, chi, C);
+    const unsigned long long m = (a << ((52 - p) & 63)) & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long bits =
+        ((unsigned long long)Y & 0x8000000000000000ull) | ((unsigned long long)e << 52) | m;
+    return __longlong_as_double(Y == 0 ? 0ll : (long long)bits);
+  } else {
+    return fixed_to_double_fp64(Y, chi, C);
+  }
+}
+
+template <bool INTCONV = false>
+__device__ __forceinline__ double exact_out(const KParams& kp, unsigned chi, double C, int y0, int y1) {
+  const long long Y = ((long long)y1 << kp.wk) + (long long)((y0 + (int)kp.rnd) >> kp.kdrop);
+  return fixed_to_double<INTCONV>(Y, chi, C);
+}
+
+template <int D, int P, int NST = 0, bool INTCONV = false>
 __device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[Pat<D, P>::M],
                                            double (&y)[Pat<D, P>::M]) {
   constexpr int M = Pat<D, P>::M;
@@ -222,7 +255,7 @@ __device__ __forceinline__ bool exact_core(const KParams& kp, const double (&x)[
   const unsigned chi = E + (unsigned)kp.cexp;
   const double C = __hiloint2double((int)chi, 0);
 #pragma unroll
-  for (int u = 0; u < M; u++) y[u] = exact_out(kp, chi, C, l0[u], l1[u]);
+  for (int u = 0; u < M; u++) y[u] = exact_out<INTCONV>(kp, chi, C, l0[u], l1[u]);
   return true;
 }
 
@@ -346,7 +379,7 @@ __device__ __forceinline__ bool exact_core_wht4(const KParams& kp, const double 
 // ---------------------------------------------------------------------------
 // one orbit element group: x (inputs, m members) -> y (outputs), incl. alpha/beta
 // ---------------------------------------------------------------------------
-template <int D, int P, int AR, typename T, int NST = 0>
+template <int D, int P, int AR, typename T, int NST = 0, bool INTCONV = false>
 __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>::M], T (&y)[Pat<D, P>::M]) {
   constexpr int M = Pat<D, P>::M;
   constexpr int NS = fact(D);
@@ -379,7 +412,7 @@ __device__ __forceinline__ void apply_group(const KParams& kp, T (&x)[Pat<D, P>:
   } else {
     bool done = false;
     if constexpr (AR == AR_EXACT) {
-      done = exact_core<D, P, NST>(kp, x, y);
+      done = exact_core<D, P, NST, INTCONV>(kp, x, y);
       if (done && (kp.flags & KF_ALPHA_MUL)) {
 #pragma unroll
         for (int u = 0; u < M; u++) y[u] = __dmul_rn(kp.alpha, y[u]);

@@ -1,6 +1,6 @@
 // Device status word and the dispatch from (d, arithmetic, vector width) to
-// the kernel instantiations of the ss_k1_*, ss_k2_*, ss_kg_* and ss_kb_*
-// translation units.
+// the kernel instantiations of the ss_k1_*, ss_k2_*, ss_kg_*, ss_kb_* and
+// ss_kc_* translation units.
 #include <cuda_runtime.h>
 
 #include "ss_devcache.h"
@@ -34,6 +34,21 @@ cudaError_t launch_kb_d4_strict(const KParams* probs, const int64_t* prefix, con
                               cudaStream_t st, const void** fn);
 cudaError_t launch_kb_d4_f32(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
                               cudaStream_t st, const void** fn);
+
+cudaError_t launch_kc_d2(const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
+                         int64_t ldc, cudaStream_t st);
+cudaError_t launch_kc_d3(const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
+                         int64_t ldc, cudaStream_t st);
+cudaError_t launch_kc_d4(const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
+                         int64_t ldc, cudaStream_t st);
+
+// the summation fused into a contraction over the permuted group (or the contraction alone)
+cudaError_t launch_kc(int d, const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
+                      int64_t ldc, cudaStream_t st) {
+  if (d == 2) return launch_kc_d2(kp, ar, sum, W, Y, ldw, C, ldc, st);
+  if (d == 3) return launch_kc_d3(kp, ar, sum, W, Y, ldw, C, ldc, st);
+  return launch_kc_d4(kp, ar, sum, W, Y, ldw, C, ldc, st);
+}
 
 cudaError_t launch_k1(int d, const KParams& kp, int ar, int vec, cudaStream_t st) {
   if (d == 2) return launch_k1_d2(kp, ar, vec, st);

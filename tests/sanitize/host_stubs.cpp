@@ -14,6 +14,9 @@ cudaError_t launch_pack(int, const KParams&, bool, bool, int, cudaStream_t) { re
 cudaError_t launch_kb(int, int, const KParams*, const int64_t*, const int*, int, int, cudaStream_t, const void**) {
   return cudaErrorNoDevice;
 }
+cudaError_t launch_kc(int, const KParams&, int, bool, const double*, int64_t, int64_t, double*, int64_t, cudaStream_t) {
+  return cudaErrorNoDevice;
+}
 int k1t_chunk(int d, int) { return d == 3 ? 512 : 256; }
 int* status_ptr() { return nullptr; }
 cudaError_t read_and_clear_status(int* out) {

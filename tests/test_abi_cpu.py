@@ -267,3 +267,42 @@ def test_pack_argument_errors_need_no_gpu(ss, case, code):
         with pytest.raises(ss.SpinsumError) as e:
             fn()
         assert e.value.status == code, (case, e.value)
+
+
+@pytest.mark.parametrize("case,code", [("bad_d", "ERR_ARG"), ("neg_y", "ERR_ARG"), ("ldw", "ERR_ARG"),
+                                       ("ldc", "ERR_ARG"), ("mode", "ERR_ARG"), ("alias_a", "ERR_ALIAS"),
+                                       ("alias_w", "ERR_ALIAS"), ("null", "ERR_ARG"), ("misaligned", "ERR_ARG")])
+def test_contract_argument_errors(ss, case, code):
+    """spinsum_contract rejects bad arguments on the host, before any launch."""
+    d, ext = 3, [4, 4, 4, 5, 5, 5]
+    S, T, Y = 64, 125, 6
+    A, W, C = FAKE_A, FAKE_B, FAKE_B + 1 << 20
+    ldw, ldc, mode, dd = Y, S, 1, d
+    if case == "bad_d":
+        dd, ext = 5, ext + [5, 5, 5, 5]
+    elif case == "neg_y":
+        Y = -1
+    elif case == "ldw":
+        ldw = Y - 1
+    elif case == "ldc":
+        ldc = S - 1
+    elif case == "mode":
+        mode = 1 | ss.SPINSUM_TMA
+    elif case == "alias_a":
+        C = A + 8 * 100
+    elif case == "alias_w":
+        C = W + 8 * 10
+    elif case == "null":
+        W = 0
+    elif case == "misaligned":
+        C += 4
+    with pytest.raises(ss.SpinsumError, match=code):
+        ss.spinsum_contract(dd, ext, A, wl.table2(1), 2, mode, W, Y, ldw, C, ldc, 0)
+    assert ss.spinsum_last_error()
+
+
+def test_contract_empty_launches_nothing(ss):
+    before = ss.spinsum_launch_count()
+    ss.spinsum_contract(3, [0, 4, 4, 5, 5, 5], FAKE_A, wl.table2(1), 2, 1, FAKE_B, 3, 3, FAKE_B + (1 << 20), 1, 0)
+    ss.spinsum_contract(3, [4, 4, 4, 5, 5, 5], FAKE_A, wl.table2(1), 2, 1, FAKE_B, 0, 1, FAKE_B + (1 << 20), 64, 0)
+    assert ss.spinsum_launch_count() == before

@@ -457,3 +457,46 @@ def test_packed_antisymmetric_storage(oracle_mod, d, O):
             for j in range(i + 1, O):
                 np.testing.assert_array_equal(B[..., i, j], P[..., i + j * (j - 1) // 2])
                 np.testing.assert_array_equal(B[..., j, i], -P[..., i + j * (j - 1) // 2])
+
+
+# ---------------------------------------------------------------------------
+# contraction over the permuted group (the fused consumer of the summation)
+# ---------------------------------------------------------------------------
+def test_contract_brute_force(oracle_mod):
+    """C[s, y] = sum over permuted tuples t of B[s, t] W[y, t], with the tuple
+    index t = i_1 + O i_2 + O^2 i_3 written out here by explicit loops."""
+    d, O, spec, Y = 3, 3, (2, 3), 4
+    A = wl.integers(40, spec + (O,) * d)
+    W = wl.integers(41, (Y, O ** d))
+    coef = wl.table2(1)
+    B = oracle_mod.spinsum(A, d, coef, factorized=True)
+    C = oracle_mod.contract(A, d, coef, W, factorized=True)
+    assert C.shape == spec + (Y,)
+    for s in itertools.product(*[range(n) for n in spec]):
+        for y in range(Y):
+            acc = 0.0
+            for t in itertools.product(range(O), repeat=d):
+                tl = t[0] + O * t[1] + O * O * t[2]
+                acc += B[s + t] * W[y, tl]
+            assert C[s + (y,)] == acc
+
+
+def test_contract_with_unit_rows_is_the_summation(oracle_mod):
+    """W = identity (Y = O^d): the contraction returns S(A) itself."""
+    d, O, spec = 4, 3, (2,)
+    A = wl.integers(42, spec + (O,) * d)
+    coef = wl.random_coef(4, 43)
+    C = oracle_mod.contract(A, d, coef, np.eye(O ** d))
+    B = oracle_mod.spinsum(A, d, coef)
+    np.testing.assert_array_equal(C, B.reshape(spec + (O ** d,), order="F"))
+
+
+def test_contract_plain_matches_tensordot(oracle_mod):
+    """coef None: the contraction alone equals numpy's tensordot over the
+    permuted axes (W reshaped column-major to one axis per index)."""
+    d, O, spec, Y = 3, 4, (3, 2), 5
+    A = wl.uniform(44, spec + (O,) * d)
+    W = wl.uniform(45, (Y, O ** d))
+    Wt = W.reshape((Y,) + (O,) * d, order="F")
+    want = np.tensordot(A, Wt, axes=([2, 3, 4], [1, 2, 3]))
+    np.testing.assert_allclose(oracle_mod.contract(A, d, None, W), want, rtol=0, atol=1e-13)
