@@ -282,6 +282,17 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_K2_MINB4
 #define SS_K2_MINB4 2
 #endif
+// K2, d = 4 through the Klein four-group transform: buffers, ids per CTA and
+// resident CTAs per SM
+#ifndef SS_K2_NBUF4W
+#define SS_K2_NBUF4W 1
+#endif
+#ifndef SS_K2_RUN4W
+#define SS_K2_RUN4W 1
+#endif
+#ifndef SS_K2_MINB4W
+#define SS_K2_MINB4W 3
+#endif
 
 // generic d = 4 orbits with a non-power-of-two alpha: 1 = an out-of-line
 // path that reloads the inputs (the common path stays 2 % faster; a
@@ -320,7 +331,12 @@ constexpr int MAXSTAGE = 8;
 constexpr int MAXSTAGE_EXACT = 3;  // the exact core unrolls at most this many stages
 constexpr int MAXSPEC = 4;
 
-enum Arith { AR_EXACT = 0, AR_STRICT = 1, AR_F32 = 2 };
+enum Arith {
+  AR_EXACT = 0,
+  AR_STRICT = 1,
+  AR_F32 = 2,
+  AR_EXACT_XW = 3,  // kernel-template choice only: AR_EXACT with d = 4 orbits through the Klein four-group transform
+};
 
 // flags
 enum {

@@ -140,16 +140,38 @@ __device__ __forceinline__ int k2_slot(int u, const int (&w)[4]) {
   return kK2Map<D, BP, EP>.bm[u] * K2Shape<D>::NT + K2Shape<D>::phys(c);
 }
 
+// the strict core for an element orbit whose exponents leave the fixed-point
+// range: rare, kept out of line so that it holds no registers in the hot path
+template <int D, int BP, int EP>
+static __device__ __noinline__ void k2_strict_group(const KParams& kp, const int* wp, double* sm) {
+  constexpr int M = Pat<D, EP>::M;
+  const int w[4] = {wp[0], wp[1], wp[2], wp[3]};
+  double x[M];
+  for (int u = 0; u < M; u++) x[u] = sm[k2_slot<D, BP, EP>(u, w)];
+  strict_core<D, EP>(kp, x);
+  for (int u = 0; u < M; u++) sm[k2_slot<D, BP, EP>(u, w)] = __dmul_rn(kp.alpha, x[u]);
+}
+
 template <int D, int BP, int EP, int AR, typename T>
 __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T* sm) {
   constexpr int M = Pat<D, EP>::M;
+  if constexpr (D == 4 && AR == AR_EXACT_XW && wht_ok<EP>()) {
+    // slots are recomputed where they are used rather than kept in registers
+    T x[M];
+#pragma unroll
+    for (int u = 0; u < M; u++) x[u] = sm[k2_slot<D, BP, EP>(u, w)];
+    auto sink = [&](int u, double v) { sm[k2_slot<D, BP, EP>(u, w)] = v; };
+    if (!exact_core_wht4<EP>(kp, x, sink)) k2_strict_group<D, BP, EP>(kp, w, sm);
+    return;
+  }
+  constexpr int ARC = AR == AR_EXACT_XW ? (int)AR_EXACT : AR;
   int s[M];
 #pragma unroll
   for (int u = 0; u < M; u++) s[u] = k2_slot<D, BP, EP>(u, w);
   T x[M];
 #pragma unroll
   for (int u = 0; u < M; u++) x[u] = sm[s[u]];
-  if constexpr (D == 4 && EP == 0 && AR == AR_EXACT) {
+  if constexpr (D == 4 && EP == 0 && ARC == AR_EXACT) {
     auto sink = [&](int u, double v) { sm[s[u]] = v; };
     if (exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) {
       if (kp.flags & KF_ALPHA_MUL) {  // alpha not a power of two: rare, a separate pass
@@ -163,7 +185,7 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
     for (int u = 0; u < M; u++) sm[s[u]] = __dmul_rn(kp.alpha, x[u]);
   } else {
     T y[M];
-    apply_group<D, EP, AR, T>(kp, x, y);
+    apply_group<D, EP, ARC, T>(kp, x, y);
 #pragma unroll
     for (int u = 0; u < M; u++) sm[s[u]] = y[u];
   }
@@ -537,9 +559,10 @@ __global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ K
 // CTAs) and SS_K2_MINB<d> resident CTAs per SM for the register budget.
 template <int D, int AR, int U, typename T>
 cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
-  constexpr int NBUF = D == 2 ? SS_K2_NBUF2 : (D == 3 ? SS_K2_NBUF3 : SS_K2_NBUF4);
-  constexpr int MINB = D == 2 ? SS_K2_MINB2 : (D == 3 ? SS_K2_MINB3 : SS_K2_MINB4);
-  constexpr int RUN = D == 2 ? SS_K2_RUN2 : (D == 3 ? SS_K2_RUN3 : SS_K2_RUN4);
+  constexpr bool XW = AR == AR_EXACT_XW;
+  constexpr int NBUF = D == 2 ? SS_K2_NBUF2 : (D == 3 ? SS_K2_NBUF3 : (XW ? SS_K2_NBUF4W : SS_K2_NBUF4));
+  constexpr int MINB = D == 2 ? SS_K2_MINB2 : (D == 3 ? SS_K2_MINB3 : (XW ? SS_K2_MINB4W : SS_K2_MINB4));
+  constexpr int RUN = D == 2 ? SS_K2_RUN2 : (D == 3 ? SS_K2_RUN3 : (XW ? SS_K2_RUN4W : SS_K2_RUN4));
   constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
   auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
   // resident CTAs per device (persistent grid), set up once per device
