@@ -302,9 +302,13 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_4D_SCALED_OUTOFLINE 1
 #endif
 
-// batched kernel (3D): resident CTAs per SM the register budget is sized for
+// batched kernel (3D): resident CTAs per SM the register budget is sized for,
+// and the most chunks a thread takes at a time (as SS_K1_KBMAX3)
 #ifndef SS_KB_MINB3
 #define SS_KB_MINB3 4
+#endif
+#ifndef SS_KB_KBMAX3
+#define SS_KB_KBMAX3 1
 #endif
 
 #ifndef SS_4D_GROUPS
@@ -312,6 +316,15 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #endif
 #ifndef SS_4D_MINBLOCKS
 #define SS_4D_MINBLOCKS 3
+#endif
+// K1 (single problems): most chunks a thread takes at a time for orbits with
+// fewer members than the generic one, for d <= 3 and d = 4 (1 = one chunk at
+// a time for every orbit; the batched kernel always takes one)
+#ifndef SS_K1_KBMAX3
+#define SS_K1_KBMAX3 2
+#endif
+#ifndef SS_K1_KBMAX4
+#define SS_K1_KBMAX4 1
 #endif
 // K1, d = 4 transform path: spectator positions per member per block
 #ifndef SS_K1_POS4

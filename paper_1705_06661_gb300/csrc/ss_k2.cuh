@@ -155,13 +155,25 @@ static __device__ __noinline__ void k2_strict_group(const KParams& kp, const int
 template <int D, int BP, int EP, int AR, typename T>
 __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T* sm) {
   constexpr int M = Pat<D, EP>::M;
-  if constexpr (D == 4 && AR == AR_EXACT_XW && wht_ok<EP>()) {
-    // slots are recomputed where they are used rather than kept in registers
+  if constexpr (D == 4 && AR == AR_EXACT_XW) {
+    // slots are recomputed where they are used rather than kept in registers;
+    // the strict core stays out of line (inlined, the compiler may predicate
+    // its FP64 operations into the common path)
     T x[M];
 #pragma unroll
     for (int u = 0; u < M; u++) x[u] = sm[k2_slot<D, BP, EP>(u, w)];
-    auto sink = [&](int u, double v) { sm[k2_slot<D, BP, EP>(u, w)] = v; };
-    if (!exact_core_wht4<EP>(kp, x, sink)) k2_strict_group<D, BP, EP>(kp, w, sm);
+    if constexpr (wht_ok<EP>()) {
+      auto sink = [&](int u, double v) { sm[k2_slot<D, BP, EP>(u, w)] = v; };
+      if (!exact_core_wht4<EP>(kp, x, sink)) k2_strict_group<D, BP, EP>(kp, w, sm);
+    } else {
+      T y[M];
+      if (exact_core<D, EP>(kp, x, y)) {
+#pragma unroll
+        for (int u = 0; u < M; u++) sm[k2_slot<D, BP, EP>(u, w)] = y[u];
+      } else {
+        k2_strict_group<D, BP, EP>(kp, w, sm);
+      }
+    }
     return;
   }
   constexpr int ARC = AR == AR_EXACT_XW ? (int)AR_EXACT : AR;

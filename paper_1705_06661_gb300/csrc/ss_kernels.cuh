@@ -527,6 +527,12 @@ static __device__ __noinline__ void scaled_generic4(const KParams& kp, const int
   if (!exact_core_grouped4<SS_4D_GROUPS>(kp, x, sink)) strict_fallback_generic4(kp, offA, offB, s);
 }
 
+// chunks a K1 thread takes at a time for an orbit of m members: the generic
+// orbit's d! over m, at most kbmax
+constexpr int k1_batch(int D, int m, int kbmax) {
+  return m >= fact(D) ? 1 : (fact(D) / m < kbmax ? fact(D) / m : kbmax);
+}
+
 // ---------------------------------------------------------------------------
 // K1 body for pattern P. Warp 0 unranks the orbit and writes the m member
 // offsets of A and B to shared memory; the CTA then streams cpb chunks of
@@ -536,7 +542,8 @@ static __device__ __noinline__ void scaled_generic4(const KParams& kp, const int
 // XW selects the Klein four-group path of d = 4 exact orbits: 0 never, 1 for
 // every transformable pattern (the planner set KF_WHT), 2 when the problem's
 // KF_WHT flag says so (batched kernels, whose problems differ).
-template <int D, int P, int AR, int VEC, typename T, int NST = 0, int XW = 0>
+// KBM: the most chunks a thread takes at a time (k1_batch).
+template <int D, int P, int AR, int VEC, typename T, int NST = 0, int XW = 0, int KBM = 1>
 __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t c0, int64_t c1) {
   constexpr int M = Pat<D, P>::M;
   __shared__ int64_t soff[2][24];
@@ -563,54 +570,99 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
   const T* A = static_cast<const T*>(kp.A);
   T* B = static_cast<T*>(kp.B);
   const int64_t step = (int64_t)blockDim.x * VEC;
-  if constexpr (D == 4 && AR == AR_EXACT && VEC == 1 && wht_ok<P>() && XW != 0) {
+  if constexpr (D == 4 && AR == AR_EXACT && VEC == 1 && XW != 0) {
     if (XW == 1 || (kp.flags & KF_WHT)) {
       const bool beta = kp.flags & KF_BETA;
-      for (int64_t c = c0; c < c1; c++) {
-        const int64_t s = c * step + (int64_t)threadIdx.x;
+      constexpr int KB = k1_batch(D, M, KBM);
+      for (int64_t c = c0; c < c1; c += KB) {
         if constexpr (SS_4DW_PREFETCH) {
-          // thread u < M asks L2 for member u's run SS_4DW_PREFETCH chunks ahead
-          const int64_t sn = (c + SS_4DW_PREFETCH) * step;
-          if (c + SS_4DW_PREFETCH < c1 && threadIdx.x < M && sn < kp.S) {
-            const int64_t n = min((int64_t)step, kp.S - sn);
+          // thread u < M asks L2 for member u's runs SS_4DW_PREFETCH batches ahead
+          const int64_t sn = (c + (int64_t)SS_4DW_PREFETCH * KB) * step;
+          if (c + SS_4DW_PREFETCH * KB < c1 && threadIdx.x < M && sn < kp.S) {
+            const int64_t n = min((int64_t)step * KB, kp.S - sn);
             const uintptr_t a = reinterpret_cast<uintptr_t>(A + soff[0][threadIdx.x] + sn);
             const unsigned bytes = (unsigned)(n * (int64_t)sizeof(T)) & ~15u;
             if ((a & 15) == 0 && bytes > 0)
               asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
           }
         }
-        if (s >= kp.S) break;
-        double x[M];
+        int64_t sk[KB];
+        bool ok[KB];
 #pragma unroll
-        for (int u = 0; u < M; u++) x[u] = A[soff[0][u] + s];
-        auto sink = [&](int u, double v) {
-          T* dst = B + soff[1][u] + s;
-          if (beta) v = add_beta(v, *dst, kp.beta);
-          *dst = v;
-        };
-        if (!exact_core_wht4<P>(kp, x, sink)) strict_fallback4<P>(kp, soff[0], soff[1], s);
+        for (int k = 0; k < KB; k++) {
+          sk[k] = (c + k) * step + (int64_t)threadIdx.x;
+          ok[k] = c + k < c1 && sk[k] < kp.S;
+        }
+        if (!ok[0]) break;
+        double x[KB][M];
+#pragma unroll
+        for (int k = 0; k < KB; k++)
+          if (ok[k]) {
+#pragma unroll
+            for (int u = 0; u < M; u++) x[k][u] = A[soff[0][u] + sk[k]];
+          }
+#pragma unroll
+        for (int k = 0; k < KB; k++) {
+          if (!ok[k]) continue;
+          const int64_t s = sk[k];
+          auto sink = [&](int u, double v) {
+            T* dst = B + soff[1][u] + s;
+            if (beta) v = add_beta(v, *dst, kp.beta);
+            *dst = v;
+          };
+          if constexpr (wht_ok<P>()) {
+            if (!exact_core_wht4<P>(kp, x[k], sink)) strict_fallback4<P>(kp, soff[0], soff[1], s);
+          } else {
+            // the two patterns V does not act on freely: the dense core on the
+            // same grid, with the strict core out of line (inlined, the compiler
+            // may predicate its FP64 operations into the common path)
+            double y[M];
+            if (exact_core<4, P>(kp, x[k], y)) {
+#pragma unroll
+              for (int u = 0; u < M; u++) sink(u, y[u]);
+            } else {
+              strict_fallback4<P>(kp, soff[0], soff[1], s);
+            }
+          }
+        }
       }
       return;
     }
   }
-  for (int64_t c = c0; c < c1; c++) {
-    const int64_t s = c * step + (int64_t)threadIdx.x * VEC;
-    if (s >= kp.S) break;
-    if constexpr (SS_4D_SCALED_OUTOFLINE && D == 4 && P == 0 && AR == AR_EXACT && VEC == 1) {
+  // orbits with fewer members than the generic one take KB chunks at a time,
+  // so that every thread has about the same number of loads in flight
+  constexpr bool G4 = D == 4 && P == 0 && AR == AR_EXACT && VEC == 1;
+  constexpr int KB = G4 ? 1 : k1_batch(D, M, KBM);
+  for (int64_t c0k = c0; c0k < c1; c0k += KB) {
+    int64_t sk[KB];
+    bool ok[KB];
+#pragma unroll
+    for (int k = 0; k < KB; k++) {
+      sk[k] = (c0k + k) * step + (int64_t)threadIdx.x * VEC;
+      ok[k] = c0k + k < c1 && sk[k] < kp.S;
+    }
+    if (!ok[0]) break;
+    const int64_t s = sk[0];
+    if constexpr (SS_4D_SCALED_OUTOFLINE && G4) {
       if (kp.flags & KF_ALPHA_MUL) {
         scaled_generic4(kp, soff[0], soff[1], s);
         continue;
       }
     }
-    T x[VEC][M], y[VEC][M];
+    T xk[KB][VEC][M];
 #pragma unroll
-    for (int u = 0; u < M; u++) {
-      T v[VEC];
-      vload<T, VEC>(A + soff[0][u] + s, v);
+    for (int k = 0; k < KB; k++)
+      if (ok[k]) {
 #pragma unroll
-      for (int e = 0; e < VEC; e++) x[e][u] = v[e];
-    }
-    if constexpr (D == 4 && P == 0 && AR == AR_EXACT && VEC == 1) {
+        for (int u = 0; u < M; u++) {
+          T v[VEC];
+          vload<T, VEC>(A + soff[0][u] + sk[k], v);
+#pragma unroll
+          for (int e = 0; e < VEC; e++) xk[k][e][u] = v[e];
+        }
+      }
+    if constexpr (G4) {
+      auto& x = xk[0];
       const bool beta = kp.flags & KF_BETA;
       bool done;
       if (!SS_4D_SCALED_OUTOFLINE && (kp.flags & KF_ALPHA_MUL)) {
@@ -632,23 +684,28 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
       if (!done) strict_fallback_generic4(kp, soff[0], soff[1], s);
       continue;
     }
-#pragma unroll
-    for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T, NST>(kp, x[e], y[e]);
     const bool beta = kp.flags & KF_BETA;
     const T bt = beta_of<T>(kp);
 #pragma unroll
-    for (int u = 0; u < M; u++) {
-      T v[VEC];
-      T* dst = B + soff[1][u] + s;
-      if (beta) {
-        vload<T, VEC>(dst, v);
+    for (int k = 0; k < KB; k++) {
+      if (!ok[k]) continue;
+      T y[VEC][M];
 #pragma unroll
-        for (int e = 0; e < VEC; e++) v[e] = add_beta(y[e][u], v[e], bt);
-      } else {
+      for (int e = 0; e < VEC; e++) apply_group<D, P, AR, T, NST>(kp, xk[k][e], y[e]);
 #pragma unroll
-        for (int e = 0; e < VEC; e++) v[e] = y[e][u];
+      for (int u = 0; u < M; u++) {
+        T v[VEC];
+        T* dst = B + soff[1][u] + sk[k];
+        if (beta) {
+          vload<T, VEC>(dst, v);
+#pragma unroll
+          for (int e = 0; e < VEC; e++) v[e] = add_beta(y[e][u], v[e], bt);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; e++) v[e] = y[e][u];
+        }
+        vstore<T, VEC>(dst, v);
       }
-      vstore<T, VEC>(dst, v);
     }
   }
 }
@@ -664,7 +721,7 @@ __device__ __forceinline__ int find_pattern(const int64_t* pre, int64_t b) {
 
 // one K1 block of work: block index b of the problem's grid -> (pattern,
 // orbit, chunk range)
-template <int D, int AR, int VEC, typename T, int XW = 0>
+template <int D, int AR, int VEC, typename T, int XW = 0, int KBM = 1>
 __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   const int p = find_pattern<D>(kp.pre, b);
   const int64_t bpo = (kp.nchunk + kp.cpb - 1) / kp.cpb;  // blocks per orbit
@@ -674,17 +731,17 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
   const int64_t c0 = cb * kp.cpb;
   const int64_t c1 = min(kp.nchunk, c0 + kp.cpb);
   switch (p) {
-    case 0: k1_body<D, 0, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-    case 1: k1_body<D, 1, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-    case 2: if constexpr (npatterns(D) > 2) k1_body<D, 2, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-    case 3: if constexpr (npatterns(D) > 3) k1_body<D, 3, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+    case 0: k1_body<D, 0, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+    case 1: k1_body<D, 1, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+    case 2: if constexpr (npatterns(D) > 2) k1_body<D, 2, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+    case 3: if constexpr (npatterns(D) > 3) k1_body<D, 3, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
     default:
       if constexpr (D == 4) {
         switch (p) {
-          case 4: k1_body<D, 4, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-          case 5: k1_body<D, 5, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-          case 6: k1_body<D, 6, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
-          case 7: k1_body<D, 7, AR, VEC, T, 0, XW>(kp, orb, c0, c1); break;
+          case 4: k1_body<D, 4, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+          case 5: k1_body<D, 5, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+          case 6: k1_body<D, 6, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
+          case 7: k1_body<D, 7, AR, VEC, T, 0, XW, KBM>(kp, orb, c0, c1); break;
         }
       }
   }
@@ -693,7 +750,7 @@ __device__ __forceinline__ void k1_block(const KParams& kp, int64_t b) {
 template <int D, int AR, int VEC, typename T, int XW = 0>
 __global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? (XW ? SS_4DW_MINBLOCKS : SS_4D_MINBLOCKS) : 1)
     k1_kernel(const __grid_constant__ KParams kp) {
-  k1_block<D, AR, VEC, T, XW>(kp, blockIdx.x);
+  k1_block<D, AR, VEC, T, XW, D <= 3 ? SS_K1_KBMAX3 : SS_K1_KBMAX4>(kp, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -706,13 +763,14 @@ __global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? (XW ? SS_4DW
 template <int D, int AR, typename T>
 __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int64_t b) {
   constexpr int VMAX = sizeof(T) == 8 ? (D <= 3 ? 2 : 1) : (D <= 3 ? 4 : 1);
+  constexpr int KBM = D <= 3 ? SS_KB_KBMAX3 : 1;
   if constexpr (VMAX >= 4) {
-    if (vec == 4) { k1_block<D, AR, 4, T>(kp, b); return; }
+    if (vec == 4) { k1_block<D, AR, 4, T, 0, KBM>(kp, b); return; }
   }
   if constexpr (VMAX >= 2) {
-    if (vec == 2) { k1_block<D, AR, 2, T>(kp, b); return; }
+    if (vec == 2) { k1_block<D, AR, 2, T, 0, KBM>(kp, b); return; }
   }
-  k1_block<D, AR, 1, T, 2>(kp, b);
+  k1_block<D, AR, 1, T, 2, KBM>(kp, b);
 }
 
 template <int D, int AR, typename T>
