@@ -922,7 +922,7 @@ int spinsum_4d_host(int dtype, const int64_t ext[8], const void* A, const int64_
 // Problems whose layout needs the general kernel are launched one by one.
 // ---------------------------------------------------------------------------
 namespace ss {
-cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                       cudaStream_t st, const void** fn);
 }
 
@@ -952,10 +952,11 @@ struct ClassRange {
 
 // bytes and field offsets of an image for n problems
 struct ImageShape {
-  size_t probs, prefix, vec, bytes;
+  size_t probs, prefix, vec, ctr, bytes;
 };
 ImageShape image_shape(int n) {
-  return ImageShape{batch_offset_probs(n), batch_offset_prefix(n), batch_offset_vec(n), batch_image_bytes(n)};
+  return ImageShape{batch_offset_probs(n), batch_offset_prefix(n), batch_offset_vec(n), batch_offset_ctr(n),
+                    batch_image_bytes(n)};
 }
 
 // Fill the image with the K1-capable launches in the given order, grouped by
@@ -1036,7 +1037,7 @@ int plan_build(spinsum_plan* P, int cpb_scale, int order, int occ, cudaStream_t 
   P->grid.clear();
   for (const ClassRange& c : P->classes) {
     const void* fn = nullptr;
-    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, 0, st, &fn);
+    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, nullptr, 0, st, &fn);
     int nb = 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
@@ -1053,10 +1054,11 @@ int plan_launch(spinsum_plan* P, cudaStream_t st) {
   const KParams* probs = reinterpret_cast<const KParams*>(P->d_image + P->shape.probs);
   const int64_t* prefix = reinterpret_cast<const int64_t*>(P->d_image + P->shape.prefix);
   const int* vec = reinterpret_cast<const int*>(P->d_image + P->shape.vec);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(P->d_image + P->shape.ctr);
   for (size_t k = 0; k < P->classes.size(); k++) {
     const ClassRange& c = P->classes[k];
-    cudaError_t e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, P->grid[k], st,
-                              nullptr);
+    cudaError_t e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, ctr + 2 * k,
+                              P->grid[k], st, nullptr);
     t_launches++;
     if (e != cudaSuccess) return cuda_fail(e, "batched kernel launch");
   }
@@ -1289,17 +1291,19 @@ extern "C" int spinsum_batch_static(const spinsum_problem* problems, int nproble
   const KParams* probs = reinterpret_cast<const KParams*>(base + sh.probs);
   const int64_t* prefix = reinterpret_cast<const int64_t*>(base + sh.prefix);
   const int* vec = reinterpret_cast<const int*>(base + sh.vec);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(dimg) + sh.ctr);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (const ClassRange& c : cls) {
+  for (size_t k = 0; k < cls.size(); k++) {
+    const ClassRange& c = cls[k];
     const void* fn = nullptr;
-    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, 0, st, &fn);
+    launch_kb(c.d, c.ar, nullptr, nullptr, nullptr, 0, nullptr, 0, st, &fn);
     int nb = 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(c.blocks, (int64_t)sms * std::max(1, nb)));
-    e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, grid, st, nullptr);
+    e = launch_kb(c.d, c.ar, probs + c.first, prefix + c.pfirst, vec + c.first, c.n, ctr + 2 * k, grid, st, nullptr);
     t_launches++;
     if (e != cudaSuccess) return cuda_fail(e, "static batched kernel launch");
   }

@@ -421,6 +421,11 @@ constexpr int BATCH_MAX_CLASSES = 12;  // (d, arithmetic) classes: 3 x 3, with r
 constexpr size_t batch_offset_vec(int n) {
   return batch_offset_prefix(n) + sizeof(int64_t) * (size_t)(n + BATCH_MAX_CLASSES);
 }
-constexpr size_t batch_image_bytes(int n) { return batch_offset_vec(n) + sizeof(int) * (size_t)n; }
+// then, 16-byte aligned, two work counters per class for the batched kernel's
+// dynamic schedule (zero between launches: the last CTA of a launch resets them)
+constexpr size_t batch_offset_ctr(int n) { return (batch_offset_vec(n) + sizeof(int) * (size_t)n + 15) / 16 * 16; }
+constexpr size_t batch_image_bytes(int n) {
+  return batch_offset_ctr(n) + 2 * sizeof(unsigned long long) * (size_t)BATCH_MAX_CLASSES;
+}
 
 }  // namespace ss

@@ -755,10 +755,15 @@ __global__ void __launch_bounds__(256, (D == 4 && AR == AR_EXACT) ? (XW ? SS_4DW
 
 // ---------------------------------------------------------------------------
 // KB: batched persistent kernel. A fixed grid walks the K1 blocks of n
-// problems with a grid stride; block g belongs to the problem i with
-// prefix[i] <= g < prefix[i + 1] (binary search). A CTA copies a problem's
-// parameters into shared memory when the problem changes, then runs that K1
-// block. One launch covers all problems of one (d, arithmetic) class.
+// problems; block g belongs to the problem i with prefix[i] <= g < prefix[i + 1]
+// (binary search). CTAs take blocks from a work counter in global memory (one
+// atomic per block), so a CTA that drew short blocks (orbits with few members,
+// small problems) simply takes more: the blocks differ in size by up to d!
+// and a fixed assignment left the grid waiting for its most loaded CTAs. A
+// CTA copies a problem's parameters into shared memory when the problem
+// changes, then runs that K1 block. One launch covers all problems of one
+// (d, arithmetic) class. ctr[0] counts blocks taken and ctr[1] CTAs done; the
+// last CTA to finish sets both back to zero for the next launch.
 // ---------------------------------------------------------------------------
 template <int D, int AR, typename T>
 __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int64_t b) {
@@ -775,11 +780,18 @@ __device__ __forceinline__ void k1_block_anyvec(const KParams& kp, int vec, int6
 
 template <int D, int AR, typename T>
 __global__ void __launch_bounds__(256, D <= 3 ? SS_KB_MINB3 : 1) kb_kernel(const KParams* __restrict__ probs, const int64_t* __restrict__ prefix,
-                                                 const int* __restrict__ vecs, int n) {
+                                                 const int* __restrict__ vecs, int n, unsigned long long* ctr) {
   __shared__ KParams skp;
-  const int64_t total = prefix[n];
+  __shared__ unsigned long long next;
+  const unsigned long long total = (unsigned long long)prefix[n];
   int cur = -1;
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(&ctr[0], 1ull);
+    __syncthreads();
+    const unsigned long long gu = next;
+    __syncthreads();  // every thread has read `next` before thread 0 overwrites it
+    if (gu >= total) break;
+    const int64_t g = (int64_t)gu;
     int lo = 0, hi = n - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -795,6 +807,15 @@ __global__ void __launch_bounds__(256, D <= 3 ? SS_KB_MINB3 : 1) kb_kernel(const
       cur = lo;
     }
     k1_block_anyvec<D, AR, T>(skp, vecs[lo], g - prefix[lo]);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr[1], 1ull) == (unsigned long long)gridDim.x - 1) {
+      // every CTA has taken its last block: nothing reads the counters again in this launch
+      ctr[0] = 0;
+      ctr[1] = 0;
+      __threadfence();
+    }
   }
 }
 

@@ -13,7 +13,7 @@ __device__ int g_status;
 cudaError_t launch_k1_d2(const KParams& kp, int ar, int vec, cudaStream_t st);
 cudaError_t launch_kg_d2(const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k2_d2(const KParams& kp, int ar, cudaStream_t st);
-cudaError_t launch_kb_d2(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb_d2(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                          cudaStream_t st, const void** fn);
 cudaError_t launch_k1_d3(const KParams& kp, int ar, int vec, cudaStream_t st);
 cudaError_t launch_k1_d4_exact(const KParams& kp, cudaStream_t st);
@@ -26,13 +26,13 @@ cudaError_t launch_k2_d4_strict(const KParams& kp, cudaStream_t st);
 cudaError_t launch_k2_d4_f32(const KParams& kp, cudaStream_t st);
 cudaError_t launch_kg_d4(const KParams& kp, int ar, cudaStream_t st);
 cudaError_t launch_k1t_d3(const KParams& kp, int ar, cudaStream_t st);
-cudaError_t launch_kb_d3(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb_d3(int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                          cudaStream_t st, const void** fn);
-cudaError_t launch_kb_d4_exact(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb_d4_exact(const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                               cudaStream_t st, const void** fn);
-cudaError_t launch_kb_d4_strict(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb_d4_strict(const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                               cudaStream_t st, const void** fn);
-cudaError_t launch_kb_d4_f32(const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb_d4_f32(const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                               cudaStream_t st, const void** fn);
 
 cudaError_t launch_kc_d2(const KParams& kp, int ar, bool sum, const double* W, int64_t Y, int64_t ldw, double* C,
@@ -101,13 +101,13 @@ cudaError_t launch_kg(int d, const KParams& kp, int ar, cudaStream_t st) {
 }
 
 // batched kernel of class (d, ar); with fn != nullptr only reports the kernel symbol
-cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, int grid,
+cudaError_t launch_kb(int d, int ar, const KParams* probs, const int64_t* prefix, const int* vecs, int n, unsigned long long* ctr, int grid,
                       cudaStream_t st, const void** fn) {
-  if (d == 2) return launch_kb_d2(ar, probs, prefix, vecs, n, grid, st, fn);
-  if (d == 3) return launch_kb_d3(ar, probs, prefix, vecs, n, grid, st, fn);
-  if (ar == AR_EXACT) return launch_kb_d4_exact(probs, prefix, vecs, n, grid, st, fn);
-  if (ar == AR_STRICT) return launch_kb_d4_strict(probs, prefix, vecs, n, grid, st, fn);
-  return launch_kb_d4_f32(probs, prefix, vecs, n, grid, st, fn);
+  if (d == 2) return launch_kb_d2(ar, probs, prefix, vecs, n, ctr, grid, st, fn);
+  if (d == 3) return launch_kb_d3(ar, probs, prefix, vecs, n, ctr, grid, st, fn);
+  if (ar == AR_EXACT) return launch_kb_d4_exact(probs, prefix, vecs, n, ctr, grid, st, fn);
+  if (ar == AR_STRICT) return launch_kb_d4_strict(probs, prefix, vecs, n, ctr, grid, st, fn);
+  return launch_kb_d4_f32(probs, prefix, vecs, n, ctr, grid, st, fn);
 }
 
 cudaError_t read_and_clear_status(int* out) {

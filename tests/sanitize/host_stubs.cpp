@@ -11,7 +11,7 @@ cudaError_t launch_k1t(int, const KParams&, int, cudaStream_t) { return cudaErro
 cudaError_t launch_k2(int, const KParams&, int, cudaStream_t) { return cudaErrorNoDevice; }
 cudaError_t launch_kg(int, const KParams&, int, cudaStream_t) { return cudaErrorNoDevice; }
 cudaError_t launch_pack(int, const KParams&, bool, bool, int, cudaStream_t) { return cudaErrorNoDevice; }
-cudaError_t launch_kb(int, int, const KParams*, const int64_t*, const int*, int, int, cudaStream_t, const void**) {
+cudaError_t launch_kb(int, int, const KParams*, const int64_t*, const int*, int, unsigned long long*, int, cudaStream_t, const void**) {
   return cudaErrorNoDevice;
 }
 cudaError_t launch_kc(int, const KParams&, int, bool, const double*, int64_t, int64_t, double*, int64_t, cudaStream_t) {
