@@ -369,8 +369,7 @@ __device__ __forceinline__ bool exact_core_wht4(const KParams& kp, const double 
 #pragma unroll
     for (int vi = 0; vi < 4; vi++) {
       const long long Y = (y4[vi] + r4) >> sh;
-      const double Dv = __hiloint2double((int)(chi + (unsigned)(Y >> 32)), (int)(unsigned)Y);
-      sink(kWht<P>.orb[o][vi], __dsub_rn(Dv, C));
+      sink(kWht<P>.orb[o][vi], fixed_to_double_fp64(Y, chi, C));
     }
   }
   return true;
