@@ -46,6 +46,19 @@ extern "C" {
 int spinsum_alg6(int d, int64_t N, const double* A, double* B, const double* coef, int nfactors,
                  int factorized, double alpha, double beta, int bl, int nthreads);
 
+/*
+ * spinsum_alg2 -- the paper's Algorithm 2 (Sec. 4.2), the spin summation of
+ * the NCC code that Algorithm 6 is measured against: loops over the sorted
+ * tuples i_1 <= ... <= i_d, and for each the d! (fewer where indices repeat)
+ * update statements of its element orbit, which share their operands. No
+ * blocking; the outermost index is split cyclically over `nthreads` threads
+ * (0: the hardware concurrency). A chain is applied as its expanded product;
+ * rounding order as above (factorized is not an option). Same layout, in
+ * place rule and return codes as spinsum_alg6.
+ */
+int spinsum_alg2(int d, int64_t N, const double* A, double* B, const double* coef, int nfactors, double alpha,
+                 double beta, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -41,7 +41,14 @@ int main() {
     for (long long i = 0; i < total; i++) scale = std::fmax(scale, std::fabs(E[i]));
     for (long long i = 0; i < total; i++)
       if (std::fabs(E[i] - F[i]) > 1e-12 * (1.0 + scale)) return 6;
+    // Algorithm 2 (expanded chain), out of place and in place, one and several threads
+    std::vector<double> G(total), H(A);
+    if (spinsum_alg2(d, N, A.data(), G.data(), coef.data(), 3, 1.0, 0.0, 1) != 0) return 7;
+    if (spinsum_alg2(d, N, H.data(), H.data(), coef.data(), 3, 1.0, 0.0, 3) != 0) return 8;
+    for (long long i = 0; i < total; i++)
+      if (G[i] != H[i] || std::fabs(E[i] - G[i]) > 1e-12 * (1.0 + scale)) return 9;
   }
+  if (spinsum_alg2(5, 2, nullptr, nullptr, nullptr, 1, 1.0, 0.0, 1) != -1) return 15;
   double A[8] = {}, B[8] = {}, c[6] = {1, 0, 0, 0, 0, 0};
   if (spinsum_alg6(1, 2, A, B, c, 1, 0, 1.0, 0.0, 0, 1) != -1) return 10;
   if (spinsum_alg6(3, 2, A, B, c, 1, 0, 1.0, 0.0, 65, 1) != -1) return 11;

@@ -92,3 +92,35 @@ def test_alg6_arguments():
         cpu_alg6.spinsum_alg6(np.zeros((4, 4, 5), order="F"), c)
     with pytest.raises(ValueError):
         cpu_alg6.spinsum_alg6(A, np.ones(5))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (the NCC code's spin summation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("d,N", [(2, 9), (2, 1), (3, 7), (3, 12), (4, 5), (4, 6)])
+def test_alg2_equals_oracle(d, N):
+    """Same rounding order as the oracle (lexicographic sigma, multiply then
+    add): equal for real single-factor sets and for integer chains (whose
+    expansion is exact)."""
+    rng = np.random.default_rng(300 + 10 * d + N)
+    n = math.factorial(d)
+    A = _uniform(rng, d, N)
+    for coef in (rng.uniform(-1.0, 1.0, (1, n)), rng.integers(-2, 3, (3, n)).astype(np.float64)):
+        for alpha, beta in ((1.0, 0.0), (0.37, -1.25)):
+            B0 = _uniform(rng, d, N)
+            want = oracle.spinsum(A, d, coef, alpha=alpha, beta=beta, B=B0.copy(order="F"))
+            for threads in (1, 3):
+                got = cpu_alg6.spinsum_alg2(A, coef, alpha=alpha, beta=beta, out=B0.copy(order="F"),
+                                            threads=threads)
+                assert np.array_equal(got, want), (d, N, alpha, beta, threads)
+
+
+@pytest.mark.parametrize("row", [1, 3, 5, 6, 18])
+def test_alg2_in_place_table2(row):
+    d = wl.table2_dim(row)
+    N = 9 if d == 3 else 5
+    A = np.asfortranarray(wl.integers(row + 50, (N,) * d))
+    coef = wl.table2(row)
+    mine = A.copy(order="F")
+    cpu_alg6.spinsum_alg2(mine, coef, inplace=True, threads=2)
+    assert np.array_equal(mine, oracle.spinsum(A, d, coef, factorized=True))

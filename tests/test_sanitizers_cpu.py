@@ -70,7 +70,7 @@ def test_host_planner_under_asan_ubsan(tmp_path, gcc):
 def test_host_alg6_under_asan_ubsan(tmp_path, gcc):
     exe = str(tmp_path / "alg6_san")
     cmd = ["g++", *SAN, "-ffp-contract=off", "-std=c++17", "-I", os.path.join(ROOT, "cpu_alg6"),
-           os.path.join(ROOT, "cpu_alg6", "alg6.cpp"),
+           os.path.join(ROOT, "cpu_alg6", "alg6.cpp"), os.path.join(ROOT, "cpu_alg6", "alg2.cpp"),
            os.path.join(ROOT, "tests", "sanitize", "alg6_driver.cpp"), "-o", exe, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0 and "sanitize" in r.stderr:
