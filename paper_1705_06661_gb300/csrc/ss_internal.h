@@ -282,6 +282,11 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_K2_MINB4
 #define SS_K2_MINB4 2
 #endif
+// K2: degenerate block orbits take their canonical offsets grouped by element
+// pattern (1) or in tile order (0)
+#ifndef SS_K2_SORTED
+#define SS_K2_SORTED 1
+#endif
 // K2, d = 4 through the Klein four-group transform: buffers, ids per CTA and
 // resident CTAs per SM
 #ifndef SS_K2_NBUF4W

@@ -44,7 +44,7 @@ struct K2Shape<2> {
   }
   // warp e / 32 takes the 16 x 2 block ((e >> 5) & 1, e >> 6) of the tile,
   // lane l its element (l & 15, l >> 4)
-  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+  __host__ __device__ static constexpr void elem(int e, int (&w)[4]) {
     const int l = e & 31, b = e >> 5;
     w[0] = (l & 15) + 16 * (b & 1);
     w[1] = (l >> 4) + 2 * (b >> 1);
@@ -63,7 +63,7 @@ struct K2Shape<3> {
   // canonical offsets of element e (0..511): warp e / 32 takes the 4x4x2 block
   // ((e >> 5) & 1, (e >> 6) & 1, e >> 7) of the tile, lane l its element
   // (l & 3, (l >> 2) & 3, l >> 4)
-  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+  __host__ __device__ static constexpr void elem(int e, int (&w)[4]) {
     const int l = e & 31, b = e >> 5;
     w[0] = (l & 3) + 4 * (b & 1);
     w[1] = ((l >> 2) & 3) + 4 * ((b >> 1) & 1);
@@ -82,7 +82,7 @@ struct K2Shape<4> {
     return x + 4 * (c[1] ^ g) + 16 * c[2] + 64 * c[3];
   }
   // warp e / 32 takes the 4x2x2x2 block (0, b & 1, (b >> 1) & 1, b >> 2) * 2
-  __device__ static __forceinline__ void elem(int e, int (&w)[4]) {
+  __host__ __device__ static constexpr void elem(int e, int (&w)[4]) {
     const int l = e & 31, b = e >> 5;
     w[0] = l & 3;
     w[1] = ((l >> 2) & 1) + 2 * (b & 1);
@@ -207,13 +207,51 @@ __device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T
 // (d = 3: bit 0 = (0,1), bit 1 = (1,2) equal; d = 4: bits (0,1), (1,2), (2,3)),
 // as a pattern index of ss_internal.h; a packed table, not a local-memory array
 template <int D>
-__device__ __forceinline__ int k2_elem_pattern(unsigned eq) {
+__host__ __device__ constexpr int k2_elem_pattern(unsigned eq) {
   if constexpr (D <= 3) {  // d = 2: bit 0 = (0,1) equal
     return (int)eq;
   } else {
     return (int)((0x76435210u >> (4 * eq)) & 0xFu);  // eq 0..7 -> 0 1 2 5 3 4 6 7
   }
 }
+
+// The canonical in-tile offsets of a block orbit of pattern BP > 0 (some
+// block coordinates equal), with their element patterns, grouped by element
+// pattern: threads take consecutive entries, so the warps of a degenerate
+// block orbit mostly run one element pattern's code (in tile order they
+// would branch into up to d! pattern bodies, each run with a few lanes).
+// Entry: w_0 .. w_3 in bytes 0..3 (w_k < 32), element pattern in bits 29..31.
+template <int D>
+struct K2List {
+  int n = 0;
+  unsigned e[1024] = {};
+};
+
+template <int D, int BP>
+constexpr K2List<D> make_k2list() {
+  using K = K2Shape<D>;
+  K2List<D> r{};
+  const Pattern<D> pb = make_pattern<D>(BP);
+  for (int ep = 0; ep < npatterns(D); ep++)
+    for (int e0 = 0; e0 < K::NT; e0++) {
+      int w[4] = {0, 0, 0, 0};
+      K::elem(e0, w);
+      bool ok = true;
+      unsigned eq = 0;
+      for (int k = 0; k + 1 < D; k++)
+        if (pb.lab[0][k] == pb.lab[0][k + 1]) {
+          ok = ok && w[k] <= w[k + 1];
+          if (w[k] == w[k + 1]) eq |= 1u << k;
+        }
+      if (!ok || k2_elem_pattern<D>(eq) != ep) continue;
+      r.e[r.n++] = (unsigned)w[0] | ((unsigned)w[1] << 8) | ((unsigned)w[2] << 16) | ((unsigned)w[3] << 24 & 0x1F000000u) |
+                   ((unsigned)ep << 29);
+    }
+  return r;
+}
+
+template <int D, int BP>
+__device__ constexpr K2List<D> kK2List = make_k2list<D, BP>();
 
 template <int D, int BP, int AR, typename T>
 __device__ __forceinline__ void k2_dispatch(const KParams& kp, int ep, const int (&w)[4], T* sm) {
@@ -469,6 +507,18 @@ __device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, 
   // pattern (compile time): for distinct blocks every offset is canonical and
   // the element pattern is the generic one
   const bool edge = T0[D - 1] * K::BL + K::BL > kp.O;  // the largest coordinate's tile is cut by the edge
+  if constexpr (BP != 0 && SS_K2_SORTED) {
+    constexpr int n = kK2List<D, BP>.n;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < n; i += 256) {
+      const unsigned pk = kK2List<D, BP>.e[i];
+      const int w[4] = {(int)(pk & 0xFFu), (int)((pk >> 8) & 0xFFu), (int)((pk >> 16) & 0xFFu),
+                        (int)((pk >> 24) & 0x1Fu)};
+      if (edge && T0[D - 1] * K::BL + w[D - 1] >= kp.O) continue;
+      k2_dispatch<D, BP, AR, T>(kp, (int)(pk >> 29), w, sm);
+    }
+    return;
+  }
 #pragma unroll 1
   for (int e0 = threadIdx.x; e0 < K::NT; e0 += 256) {
     int w[4];
