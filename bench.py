@@ -511,8 +511,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     dt_e2e = allmax(world, time_steps(e2e_step, e2e_steps, stream, world))
     e2e_val = world * bytes_step * e2e_steps / dt_e2e / 1e9
-    # the result that came back is the device result
-    assert torch.equal(B_pin[(slice(0, 2),) * nd], B[(slice(0, 2),) * nd].cpu())
+    # the result that came back is the device result (B holds it unless the
+    # timed step was the contraction profiling case)
+    if not args.case.startswith("contract"):
+        assert torch.equal(B_pin[(slice(0, 2),) * nd], B[(slice(0, 2),) * nd].cpu())
 
     # ---- extra cases: other modes and the 4D workload (not the headline) ----
     extra = []
