@@ -48,8 +48,8 @@ CASES = {
     # the paper's own layout: a dense N^d tensor, every index permuted (tiled kernel)
     "paper-3d": (3, (344,) * 3, 1),
     "paper-4d": (4, (80,) * 4, 5),
-    # the summation fused into a contraction with W[8, 16^3] (FP64-pipe-bound kernel)
-    "contract-small": (3, (24, 24, 24, 16, 16, 16), 1),
+    # the summation fused into a contraction with W[8, 8^3] (FP64-pipe-bound kernel)
+    "contract-small": (3, (48, 48, 48, 8, 8, 8), 1),
 }
 CONTRACT_Y = 8
 

@@ -340,6 +340,10 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_4DW_PREFETCH
 #define SS_4DW_PREFETCH 1
 #endif
+// ... with an evict-last L2 policy on the prefetched lines (1)
+#ifndef SS_4DW_PFHINT
+#define SS_4DW_PFHINT 1
+#endif
 // the same for the K1 kernel of d = 4 orbits through the Klein four-group transform
 #ifndef SS_4DW_MINBLOCKS
 #define SS_4DW_MINBLOCKS 3

@@ -581,8 +581,17 @@ __device__ __forceinline__ void k1_body(const KParams& kp, int64_t orb, int64_t 
             const int64_t n = min((int64_t)step * KB, kp.S - sn);
             const uintptr_t a = reinterpret_cast<uintptr_t>(A + soff[0][threadIdx.x] + sn);
             const unsigned bytes = (unsigned)(n * (int64_t)sizeof(T)) & ~15u;
-            if ((a & 15) == 0 && bytes > 0)
-              asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+            if ((a & 15) == 0 && bytes > 0) {
+              if constexpr (SS_4DW_PFHINT) {
+                unsigned long long pol;
+                asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+                asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a), "r"(bytes),
+                             "l"(pol)
+                             : "memory");
+              } else {
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
+              }
+            }
           }
         }
         int64_t sk[KB];
