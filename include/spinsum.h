@@ -241,7 +241,10 @@ int spinsum_pack(int d, int dtype, const int64_t ext[], const void* B, const int
  * valid and in-place problems are restored only if `allow_tuning_runs` is 0,
  * in which case a fixed heuristic is used). dtype applies to all problems.
  * spinsum_plan_execute launches the whole batch as one kernel on `stream`;
- * it allocates nothing and may be captured in a CUDA graph.
+ * it allocates nothing and may be captured in a CUDA graph. The kernel's CTAs
+ * take work from counters in the plan's device memory (the last CTA of a
+ * launch resets them), so two executions of one plan must not overlap on the
+ * GPU; distinct plans are independent.
  */
 typedef struct spinsum_problem {
   int d;            /* 2, 3 or 4 */
@@ -277,7 +280,7 @@ const char* spinsum_plan_describe(const spinsum_plan* plan);
  * synchronization it can imply) may not happen on the request path. For them
  * this entry point runs the same batched kernel as a plan, but reads the
  * per-problem parameters and block prefix sums from one fixed array that the
- * library keeps in device memory from load until process exit (about 400 KB
+ * library keeps in device memory from load until process exit (about 430 KB
  * on every GPU that loads the library). The caller still owns and passes every
  * input and output tensor.
  *
