@@ -316,6 +316,15 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_KB_KBMAX3 1
 #endif
 
+// K2: the beta term of the copy-out in an out-of-line call (1) or inline (0)
+#ifndef SS_K2_BETA_CALL
+#define SS_K2_BETA_CALL 1
+#endif
+// K2, d = 4 through the Klein four-group transform: slots of the generic
+// orbit's members from a per-thread table in shared memory (1) or recomputed (0)
+#ifndef SS_K2_SLOTS4
+#define SS_K2_SLOTS4 1
+#endif
 #ifndef SS_4D_GROUPS
 #define SS_4D_GROUPS 3
 #endif

@@ -140,6 +140,12 @@ __device__ __forceinline__ int k2_slot(int u, const int (&w)[4]) {
   return kK2Map<D, BP, EP>.bm[u] * K2Shape<D>::NT + K2Shape<D>::phys(c);
 }
 
+// whether the kernel keeps a slot table for the generic orbits (d = 4, transform core)
+template <int D, int AR>
+__host__ __device__ constexpr bool k2_slot_table() {
+  return SS_K2_SLOTS4 && D == 4 && AR == AR_EXACT_XW;
+}
+
 // the strict core for an element orbit whose exponents leave the fixed-point
 // range: rare, kept out of line so that it holds no registers in the hot path
 template <int D, int BP, int EP>
@@ -153,17 +159,24 @@ static __device__ __noinline__ void k2_strict_group(const KParams& kp, const int
 }
 
 template <int D, int BP, int EP, int AR, typename T>
-__device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T* sm) {
+__device__ __forceinline__ void k2_group(const KParams& kp, const int (&w)[4], T* sm,
+                                         const unsigned short* sl = nullptr) {
   constexpr int M = Pat<D, EP>::M;
   if constexpr (D == 4 && AR == AR_EXACT_XW) {
-    // slots are recomputed where they are used rather than kept in registers;
-    // the strict core stays out of line (inlined, the compiler may predicate
-    // its FP64 operations into the common path)
+    // slots are recomputed where they are used rather than kept in registers
+    // (the generic orbit of a generic block orbit reads them from the
+    // thread's column of the slot table sl when there is one); the strict
+    // core stays out of line (inlined, the compiler may predicate its FP64
+    // operations into the common path)
+    auto slot = [&](int u) {
+      if constexpr (BP == 0 && EP == 0 && SS_K2_SLOTS4) return (int)sl[u * 256 + threadIdx.x];
+      else return k2_slot<D, BP, EP>(u, w);
+    };
     T x[M];
 #pragma unroll
-    for (int u = 0; u < M; u++) x[u] = sm[k2_slot<D, BP, EP>(u, w)];
+    for (int u = 0; u < M; u++) x[u] = sm[slot(u)];
     if constexpr (wht_ok<EP>()) {
-      auto sink = [&](int u, double v) { sm[k2_slot<D, BP, EP>(u, w)] = v; };
+      auto sink = [&](int u, double v) { sm[slot(u)] = v; };
       if (!exact_core_wht4<EP>(kp, x, sink)) k2_strict_group<D, BP, EP>(kp, w, sm);
     } else {
       T y[M];
@@ -416,6 +429,20 @@ __device__ __forceinline__ void k2_next(const KParams& kp, int64_t id, int64_t s
   if ((threadIdx.x & 31) == 0) dsc.bp = -1;
 }
 
+// a stored unit with the beta term (U elements v0, v1 at g), out of line:
+// inlined, the compiler may predicate its FP64 operations into the common
+// beta = 0 path, where they would still occupy the FP64 pipe
+template <typename T, int U>
+static __device__ __noinline__ void k2_store_beta(T* g, T v0, T v1, T bt) {
+  T v[U], o[U];
+  v[0] = v0;
+  if constexpr (U == 2) v[1] = v1;
+  vload<T, U>(g, o);
+#pragma unroll
+  for (int i = 0; i < U; i++) v[i] = add_beta(v[i], o[i], bt);
+  vstore<T, U>(g, v);
+}
+
 // Copy the m_b tiles of a block orbit between HBM and shared memory in units
 // of U elements along the stride-1 index (U = 2: 16 bytes for FP64, 8 for
 // FP32; U = 1 where the tensor's strides or base addresses do not allow
@@ -483,6 +510,12 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
         } else {
           v[0] = sp[0];
         }
+#if SS_K2_BETA_CALL
+        if (beta)
+          k2_store_beta<T, U>(g, v[0], v[U - 1], bt);
+        else
+          vstore<T, U>(g, v);
+#else
         if (beta) {
           T o[U];
           vload<T, U>(g, o);
@@ -490,6 +523,7 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
           for (int i = 0; i < U; i++) v[i] = add_beta(v[i], o[i], bt);
         }
         vstore<T, U>(g, v);
+#endif
       }
     }
   }
@@ -498,7 +532,7 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
 // the element orbits of one block orbit of pattern BP, in shared memory: each
 // thread takes canonical in-tile offsets w of the first tile member
 template <int D, int BP, int AR, typename T>
-__device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, T* sm) {
+__device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, T* sm, const unsigned short* sl) {
   using K = K2Shape<D>;
   int T0[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -534,7 +568,7 @@ __device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, 
     }
     if (!ok) continue;
     if constexpr (BP == 0) {
-      if constexpr (kK2Map<D, BP, 0>.valid) k2_group<D, BP, 0, AR, T>(kp, w, sm);
+      if constexpr (kK2Map<D, BP, 0>.valid) k2_group<D, BP, 0, AR, T>(kp, w, sm, sl);
     } else {
       k2_dispatch<D, BP, AR, T>(kp, k2_elem_pattern<D>(eq), w, sm);
     }
@@ -542,19 +576,19 @@ __device__ __forceinline__ void k2_orbits(const KParams& kp, const K2Desc& dsc, 
 }
 
 template <int D, int AR, typename T>
-__device__ __forceinline__ void k2_compute(const KParams& kp, const K2Desc& dsc, T* sm) {
+__device__ __forceinline__ void k2_compute(const KParams& kp, const K2Desc& dsc, T* sm, const unsigned short* sl) {
   switch (dsc.bp) {
-    case 0: k2_orbits<D, 0, AR, T>(kp, dsc, sm); break;
-    case 1: k2_orbits<D, 1, AR, T>(kp, dsc, sm); break;
-    case 2: if constexpr (npatterns(D) > 2) k2_orbits<D, 2, AR, T>(kp, dsc, sm); break;
-    case 3: if constexpr (npatterns(D) > 3) k2_orbits<D, 3, AR, T>(kp, dsc, sm); break;
+    case 0: k2_orbits<D, 0, AR, T>(kp, dsc, sm, sl); break;
+    case 1: k2_orbits<D, 1, AR, T>(kp, dsc, sm, sl); break;
+    case 2: if constexpr (npatterns(D) > 2) k2_orbits<D, 2, AR, T>(kp, dsc, sm, sl); break;
+    case 3: if constexpr (npatterns(D) > 3) k2_orbits<D, 3, AR, T>(kp, dsc, sm, sl); break;
     default:
       if constexpr (D == 4) {
         switch (dsc.bp) {
-          case 4: k2_orbits<D, 4, AR, T>(kp, dsc, sm); break;
-          case 5: k2_orbits<D, 5, AR, T>(kp, dsc, sm); break;
-          case 6: k2_orbits<D, 6, AR, T>(kp, dsc, sm); break;
-          case 7: k2_orbits<D, 7, AR, T>(kp, dsc, sm); break;
+          case 4: k2_orbits<D, 4, AR, T>(kp, dsc, sm, sl); break;
+          case 5: k2_orbits<D, 5, AR, T>(kp, dsc, sm, sl); break;
+          case 6: k2_orbits<D, 6, AR, T>(kp, dsc, sm, sl); break;
+          case 7: k2_orbits<D, 7, AR, T>(kp, dsc, sm, sl); break;
         }
       }
   }
@@ -574,6 +608,18 @@ __global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ K
   extern __shared__ __align__(16) unsigned char k2_smem[];
   T* const buf0 = reinterpret_cast<T*>(k2_smem);
   T* const buf1 = buf0 + (NBUF > 1 ? fact(D) * K::NT : 0);
+  // d = 4 transform instantiation: after the buffers, each thread's slots of
+  // the members of its generic orbit (in-tile offset of element threadIdx.x)
+  // in a generic block orbit, one column per thread; read back only by the
+  // same thread, so no barrier
+  constexpr bool SLT = k2_slot_table<D, AR>();
+  unsigned short* const sl = SLT ? reinterpret_cast<unsigned short*>(buf0 + NBUF * fact(D) * K::NT) : nullptr;
+  if constexpr (SLT) {
+    int w[4];
+    K::elem(threadIdx.x, w);
+#pragma unroll
+    for (int u = 0; u < 24; u++) sl[u * 256 + threadIdx.x] = (unsigned short)k2_slot<4, 0, 0>(u, w);
+  }
   __shared__ K2Desc dsc[3];
   const bool w0 = threadIdx.x < 32;
   // ids of this CTA: a run of RUN consecutive ids, or (RUN = 0) every
@@ -605,7 +651,7 @@ __global__ void __launch_bounds__(256, MINB) k2_kernel(const __grid_constant__ K
       cp_async_wait<0>();
     }
     __syncthreads();
-    k2_compute<D, AR, T>(kp, cur, cb);
+    k2_compute<D, AR, T>(kp, cur, cb, sl);
     __syncthreads();
     k2_copy<D, U, false, T>(kp, cb, cur);
     if constexpr (NBUF == 1) {
@@ -625,7 +671,8 @@ cudaError_t launch_k2_vec(const KParams& kp, cudaStream_t st) {
   constexpr int NBUF = D == 2 ? SS_K2_NBUF2 : (D == 3 ? SS_K2_NBUF3 : (XW ? SS_K2_NBUF4W : SS_K2_NBUF4));
   constexpr int MINB = D == 2 ? SS_K2_MINB2 : (D == 3 ? SS_K2_MINB3 : (XW ? SS_K2_MINB4W : SS_K2_MINB4));
   constexpr int RUN = D == 2 ? SS_K2_RUN2 : (D == 3 ? SS_K2_RUN3 : (XW ? SS_K2_RUN4W : SS_K2_RUN4));
-  constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T);
+  constexpr size_t smem = (size_t)NBUF * fact(D) * K2Shape<D>::NT * sizeof(T) +
+                          (k2_slot_table<D, AR>() ? 24 * 256 * sizeof(unsigned short) : 0);
   auto fn = k2_kernel<D, AR, U, NBUF, RUN, MINB, T>;
   // resident CTAs per device (persistent grid), set up once per device
   static DeviceCache cache;
