@@ -237,8 +237,6 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_K1T4_NST 3
 #endif
 
-// 4D generic orbit in the exact core: outputs per register group (24 / G)
-// and the CTAs per SM the kernel is compiled for
 // K2 CTA grouping: log2 of the tiles per coarse-block edge (2D / 3D / 4D)
 #ifndef SS_K2_LF2
 #define SS_K2_LF2 0
@@ -247,7 +245,7 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_K2_LF3 1
 #endif
 #ifndef SS_K2_LF4
-#define SS_K2_LF4 2
+#define SS_K2_LF4 1
 #endif
 // K2: buffers of d! tiles per CTA (2 = the next block orbit is copied while the
 // current one is computed) and resident CTAs per SM the register budget is
@@ -325,6 +323,8 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_K2_SLOTS4
 #define SS_K2_SLOTS4 1
 #endif
+// 4D generic orbit in the exact core: outputs per register group (24 / G)
+// and the CTAs per SM the kernel is compiled for
 #ifndef SS_4D_GROUPS
 #define SS_4D_GROUPS 3
 #endif
