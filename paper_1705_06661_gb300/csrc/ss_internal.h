@@ -323,6 +323,11 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #ifndef SS_K2_SLOTS4
 #define SS_K2_SLOTS4 1
 #endif
+// K2: block orbits whose tiles are all full copied by an unrolled loop
+// without bounds checks (d <= 3)
+#ifndef SS_K2_COPY_FULL
+#define SS_K2_COPY_FULL 1
+#endif
 // 4D generic orbit in the exact core: outputs per register group (24 / G)
 // and the CTAs per SM the kernel is compiled for
 #ifndef SS_4D_GROUPS

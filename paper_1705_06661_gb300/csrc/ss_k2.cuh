@@ -309,6 +309,7 @@ struct K2Desc {
   unsigned char full[24];
   int64_t id;
   int bp, mb;
+  int allfull;  // every tile of the block orbit is a full tile
   int val[4];
 };
 
@@ -323,9 +324,9 @@ __device__ __forceinline__ void k2_fill(const KParams& kp, const int (&val)[4], 
     dsc.mb = MB;
   }
   if (u < D) dsc.val[u] = u == 0 ? val[0] : (u == 1 ? val[1] : (u == 2 ? val[2] : val[3]));
+  bool full = true;
   if (u < MB) {
     int64_t oa = 0, ob = 0;
-    bool full = true;
 #pragma unroll
     for (int k = 0; k < D; k++) {
       const int l = kPattern<D, BP>.lab[u][k];  // selects, not a local-memory index
@@ -339,6 +340,8 @@ __device__ __forceinline__ void k2_fill(const KParams& kp, const int (&val)[4], 
     dsc.base[1][u] = ob;
     dsc.full[u] = full;
   }
+  const unsigned part = __ballot_sync(0xffffffffu, !full);
+  if (u == 0) dsc.allfull = part == 0;
 }
 
 // Colex unranking as in unrank(), by a whole warp at once: the candidates c of
@@ -488,6 +491,50 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
   T* G = LOAD ? const_cast<T*>(static_cast<const T*>(kp.A)) : static_cast<T*>(kp.B);
   const bool beta = !LOAD && (kp.flags & KF_BETA);
   const T bt = beta_of<T>(kp);
+  auto unit = [&](int u, int q) {
+    T* g = G + base[u] + goff[q];
+    T* sp = sm + u * K::NT + slot[q];
+    if constexpr (LOAD) {
+      cp_async<U * sizeof(T)>(sp, g);
+    } else {
+      T v[U];
+      if constexpr (U == 2) {
+        vload<T, 2>(sp, v);
+      } else {
+        v[0] = sp[0];
+      }
+#if SS_K2_BETA_CALL
+      if (beta)
+        k2_store_beta<T, U>(g, v[0], v[U - 1], bt);
+      else
+        vstore<T, U>(g, v);
+#else
+      if (beta) {
+        T o[U];
+        vload<T, U>(g, o);
+#pragma unroll
+        for (int i = 0; i < U; i++) v[i] = add_beta(v[i], o[i], bt);
+      }
+      vstore<T, U>(g, v);
+#endif
+    }
+  };
+#if SS_K2_COPY_FULL
+  // d <= 3, every tile full (all block orbits away from the upper edge): the
+  // m_b <= d! tiles unrolled, no bounds checks
+  if constexpr (D <= 3 && TPP == 1) {
+    if (dsc.allfull) {
+#pragma unroll
+      for (int u = 0; u < fact(D); u++) {
+        if (u < mb) {
+#pragma unroll
+          for (int q = 0; q < NCH; q++) unit(u, q);
+        }
+      }
+      return;
+    }
+  }
+#endif
   for (int u = u0; u < mb; u += TPP) {
     const bool full_u = dsc.full[u];
 #pragma unroll
@@ -499,32 +546,7 @@ __device__ __forceinline__ void k2_copy(const KParams& kp, T* sm, const K2Desc& 
         for (int k = 0; k < D; k++) in = in && w[q][k] < dsc.lim[u][k];
       }
       if (!in) continue;
-      T* g = G + base[u] + goff[q];
-      T* sp = sm + u * K::NT + slot[q];
-      if constexpr (LOAD) {
-        cp_async<U * sizeof(T)>(sp, g);
-      } else {
-        T v[U];
-        if constexpr (U == 2) {
-          vload<T, 2>(sp, v);
-        } else {
-          v[0] = sp[0];
-        }
-#if SS_K2_BETA_CALL
-        if (beta)
-          k2_store_beta<T, U>(g, v[0], v[U - 1], bt);
-        else
-          vstore<T, U>(g, v);
-#else
-        if (beta) {
-          T o[U];
-          vload<T, U>(g, o);
-#pragma unroll
-          for (int i = 0; i < U; i++) v[i] = add_beta(v[i], o[i], bt);
-        }
-        vstore<T, U>(g, v);
-#endif
-      }
+      unit(u, q);
     }
   }
 }
