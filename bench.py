@@ -48,6 +48,9 @@ CASES = {
     # the paper's own layout: a dense N^d tensor, every index permuted (tiled kernel)
     "paper-3d": (3, (344,) * 3, 1),
     "paper-4d": (4, (80,) * 4, 5),
+    # the same at the sizes of the default run's paper-layout lines (one-pass captures only)
+    "paper-3d-544": (3, (544,) * 3, 1),
+    "paper-4d-112": (4, (112,) * 4, 5),
     # the summation fused into a contraction with W[8, 8^3] (FP64-pipe-bound kernel)
     "contract-small": (3, (48, 48, 48, 8, 8, 8), 1),
 }
@@ -161,6 +164,7 @@ KERNEL_SOURCES = {
     "kc": ("ss_internal.h", "ss_kernels.cuh", "ss_contract.cuh", "ss_kc_d3.cu", "ss_host.cpp", "ss_status.cu"),
 }
 CASE_KERNEL = {"3d": "k1", "3d-small": "k1", "4d": "k1", "4d-small": "k1", "paper-3d": "k2", "paper-4d": "k2",
+               "paper-3d-544": "k2", "paper-4d-112": "k2",
                "contract-small": "kc"}
 
 

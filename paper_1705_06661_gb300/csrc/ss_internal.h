@@ -245,7 +245,7 @@ constexpr int MP_MAX = MP_TOTAL_4;
 #define SS_K2_LF3 1
 #endif
 #ifndef SS_K2_LF4
-#define SS_K2_LF4 1
+#define SS_K2_LF4 2
 #endif
 // K2: buffers of d! tiles per CTA (2 = the next block orbit is copied while the
 // current one is computed) and resident CTAs per SM the register budget is
